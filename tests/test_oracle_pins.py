@@ -1,0 +1,460 @@
+"""Pins of the FP64 CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against a fact that does not come from the
+oracle itself: lattice isotropy and Hermite orthogonality, the equilibrium and
+source-term moment identities the paper derives (sumfeq, sumGi), conservation
+by the collision, exact special cases (tau = 1, uniform states), symmetry of
+the lattice, the Poiseuille closed form of Sec. II D (eq_a3 with the slip of
+eq_a28), Couette flow, the Taylor-Green decay of Sec. III B, and the force
+balance of a steady channel.  Everything here runs on the CPU.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_10318_gb300 import params as P
+from paper_2312_10318_gb300 import workloads as W
+
+CS2 = 1.0 / 3.0
+RNG = np.random.default_rng(1234)
+
+
+def _delta(a, b):
+    return 1.0 if a == b else 0.0
+
+
+# ---------------------------------------------------------------- lattice, eq3
+
+def test_lattice_isotropy():
+    """D2Q9 weights and velocities (Sec. II B): sum w = 1, sum w e_a e_b = c_s^2 delta,
+    sum w e_a e_b e_c e_d = c_s^4 (dd + dd + dd), odd moments vanish."""
+    e, w, cs2 = O.lattice()
+    assert cs2 == pytest.approx(1.0 / 3.0, abs=1e-16)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    for a, b in itertools.product(range(2), repeat=2):
+        assert (w * e[:, a] * e[:, b]).sum() == pytest.approx(CS2 * _delta(a, b), abs=1e-15)
+    for a, b, c, d in itertools.product(range(2), repeat=4):
+        iso = CS2 ** 2 * (_delta(a, b) * _delta(c, d) + _delta(a, c) * _delta(b, d) + _delta(a, d) * _delta(b, c))
+        assert (w * e[:, a] * e[:, b] * e[:, c] * e[:, d]).sum() == pytest.approx(iso, abs=1e-15)
+    for a in range(2):
+        assert (w * e[:, a]).sum() == 0.0
+    # opposite velocities exist for every direction
+    for i in range(9):
+        assert any((e[j] == -e[i]).all() for j in range(9))
+
+
+def test_hermite_definitions_and_d2q9_identities():
+    """eq3 built from e and c_s, and the D2Q9 identities printed after it:
+    H_xxx = H_yyy = 0, H_xxy = H_xx e_y, H_xyy = H_yy e_x."""
+    e, w, _ = O.lattice()
+    for i in range(9):
+        h1, h2, h3 = O.hermite(i)
+        assert np.array_equal(h1, e[i].astype(float))
+        assert h2[0, 0] == pytest.approx(e[i, 0] ** 2 - CS2, abs=1e-16)
+        assert h2[0, 1] == e[i, 0] * e[i, 1]
+        assert h3[0, 0, 0] == pytest.approx(0.0, abs=1e-16)
+        assert h3[1, 1, 1] == pytest.approx(0.0, abs=1e-16)
+        assert h3[0, 0, 1] == pytest.approx(h2[0, 0] * e[i, 1], abs=1e-16)
+        assert h3[0, 1, 1] == pytest.approx(h2[1, 1] * e[i, 0], abs=1e-16)
+        # full symmetry of the tensors
+        for p in itertools.permutations(range(3)):
+            assert np.allclose(h3, np.transpose(h3, p), atol=1e-16)
+
+
+def test_hermite_orthogonality():
+    """Weighted orthogonality of the Hermite polynomials on D2Q9, which makes
+    the regularized reconstruction of eq2 invert the projections of eq9."""
+    e, w, _ = O.lattice()
+    H = [O.hermite(i) for i in range(9)]
+    h0 = np.ones(9)
+    h1 = np.array([H[i][0] for i in range(9)])
+    h2 = np.array([H[i][1] for i in range(9)])
+    h3 = np.array([H[i][2] for i in range(9)])
+    assert np.abs(np.einsum("i,i,ia->a", w, h0, h1)).max() < 1e-16
+    assert np.abs(np.einsum("i,i,iab->ab", w, h0, h2)).max() < 1e-16
+    assert np.abs(np.einsum("i,ia,ibc->abc", w, h1, h2)).max() < 1e-16
+    assert np.abs(np.einsum("i,iab,icde->abcde", w, h2, h3)).max() < 1e-16
+    assert np.abs(np.einsum("i,ia,ibcd->abcd", w, h1, h3)).max() < 1e-16
+    g22 = np.einsum("i,iab,icd->abcd", w, h2, h2)
+    for a, b, c, d in itertools.product(range(2), repeat=4):
+        assert g22[a, b, c, d] == pytest.approx(CS2 ** 2 * (_delta(a, c) * _delta(b, d) + _delta(a, d) * _delta(b, c)), abs=1e-16)
+    g33 = np.einsum("i,iabc,idef->abcdef", w, h3, h3)
+    # xxy with xxy: c_s^6 * 2 (the pairings that D2Q9 keeps)
+    assert g33[0, 0, 1, 0, 0, 1] == pytest.approx(2 * CS2 ** 3, abs=1e-16)
+    assert g33[0, 1, 1, 0, 1, 1] == pytest.approx(2 * CS2 ** 3, abs=1e-16)
+    assert g33[0, 0, 1, 0, 1, 1] == pytest.approx(0.0, abs=1e-16)
+
+
+# ------------------------------------------------------------- eq4, sumfeq
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments(seed):
+    """sumfeq: sum f^eq = rho, sum e f^eq = rho u, sum e e f^eq = rho u u + rho c_s^2 delta,
+    sum e e e f^eq = rho u u u + rho c_s^2 u_z Delta_abgz - Phi_abg (Phi = rho u_a^3 on the diagonal)."""
+    r = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * r.uniform(-1, 1)
+    u = 0.1 * r.uniform(-1, 1, 2)
+    feq = O.equilibrium(rho, u)
+    e, _, _ = O.lattice()
+    assert feq.sum() == pytest.approx(rho, abs=1e-15)
+    for a in range(2):
+        assert (e[:, a] * feq).sum() == pytest.approx(rho * u[a], abs=1e-15)
+        for b in range(2):
+            assert (e[:, a] * e[:, b] * feq).sum() == pytest.approx(rho * u[a] * u[b] + rho * CS2 * _delta(a, b), abs=1e-15)
+            for c in range(2):
+                Delta = sum(u[z] * (_delta(a, b) * _delta(c, z) + _delta(a, c) * _delta(b, z) + _delta(a, z) * _delta(b, c)) for z in range(2))
+                Phi = rho * u[a] ** 3 if a == b == c else 0.0
+                want = rho * u[a] * u[b] * u[c] + rho * CS2 * Delta - Phi
+                assert (e[:, a] * e[:, b] * e[:, c] * feq).sum() == pytest.approx(want, abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_source_term_moments(seed):
+    """sumGi: sum G = 0, sum e G = 0, sum e e G = -(1 - 1/(2 tau1)) d_g Phi_abg;
+    sum F_i = 0, sum e F_i = F, sum e e F_i = F u + u F."""
+    r = np.random.default_rng(100 + seed)
+    tau1 = 0.5 + r.uniform(0.01, 3)
+    dphi = np.zeros((2, 2))
+    dphi[0, 0], dphi[1, 1] = r.uniform(-1e-3, 1e-3, 2)
+    G = O.compensation(tau1, dphi)
+    F = r.uniform(-1e-3, 1e-3, 2)
+    u = r.uniform(-0.1, 0.1, 2)
+    Fi = O.forcing(F, u)
+    e, _, _ = O.lattice()
+    assert abs(G.sum()) < 1e-18 and abs(Fi.sum()) < 1e-18
+    for a in range(2):
+        assert abs((e[:, a] * G).sum()) < 1e-18
+        assert (e[:, a] * Fi).sum() == pytest.approx(F[a], abs=1e-18)
+        for b in range(2):
+            assert (e[:, a] * e[:, b] * G).sum() == pytest.approx(-(1 - 1 / (2 * tau1)) * dphi[a, b], abs=1e-18)
+            assert (e[:, a] * e[:, b] * Fi).sum() == pytest.approx(F[a] * u[b] + u[a] * F[b], abs=1e-18)
+
+
+def _node_params(tau1, tau2, g=(0.0, 0.0)):
+    return O.Params(nx=1, ny=1, tau1=tau1, tau2=tau2, gx=g[0], gy=g[1])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_collision_conservation_and_first_projection(seed):
+    """Mass and momentum under the collision of eq2 to 1e-14: sum f* = sum f and
+    sum e f* = sum e f + F; and A_a^neq = -F_a/2 for any state (eq11, eq9)."""
+    r = np.random.default_rng(200 + seed)
+    tau1, tau2 = 0.5 + r.uniform(0.001, 5), 0.5 + r.uniform(0.001, 5)
+    g = r.uniform(-1e-3, 1e-3, 2)
+    f = W.random_populations(1, 1, seed=seed).reshape(9)
+    dphi = np.diag(r.uniform(-1e-4, 1e-4, 2))
+    out = O.collide_node(_node_params(tau1, tau2, g), f, dphi)
+    e, _, _ = O.lattice()
+    rho = f.sum()
+    assert abs(out["fstar"].sum() - rho) < 1e-14
+    for a in range(2):
+        assert abs((e[:, a] * out["fstar"]).sum() - ((e[:, a] * f).sum() + rho * g[a])) < 1e-14
+    A1, _, _ = O.projections(f, out["feq"])
+    assert np.allclose(A1, -0.5 * rho * g, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_collision_relaxes_each_hermite_order(seed):
+    """Orthogonality makes eq2 act order by order: the post-collision
+    non-equilibrium second moments are (1 - 1/tau1) A_ab + (1 - 1/(2 tau1))(F u + u F
+    - d Phi), the third ones (xxy, xyy) are (1 - 1/tau2) A_abg."""
+    r = np.random.default_rng(300 + seed)
+    tau1, tau2 = 0.5 + r.uniform(0.01, 4), 0.5 + r.uniform(0.01, 4)
+    g = r.uniform(-1e-3, 1e-3, 2)
+    f = W.random_populations(1, 1, seed=50 + seed).reshape(9)
+    dphi = np.diag(r.uniform(-1e-4, 1e-4, 2))
+    out = O.collide_node(_node_params(tau1, tau2, g), f, dphi)
+    _, A2, A3 = O.projections(f, out["feq"])
+    _, B2, B3 = O.projections(out["fstar"], out["feq"])
+    rho, u = out["rho"], out["u"]
+    F = rho * g
+    kf = 1 - 1 / (2 * tau1)
+    for a, b in itertools.product(range(2), repeat=2):
+        want = (1 - 1 / tau1) * A2[a, b] + kf * (F[a] * u[b] + u[a] * F[b]) - kf * dphi[a, b]
+        assert B2[a, b] == pytest.approx(want, abs=1e-15)
+    for idx in [(0, 0, 1), (0, 1, 1)]:
+        assert B3[idx] == pytest.approx((1 - 1 / tau2) * A3[idx], abs=1e-15)
+
+
+def test_unit_relaxation_times_give_equilibrium_plus_sources():
+    """tau1 = tau2 = 1 removes every relaxation term of eq2: f* = f^eq + G + F_i / 2."""
+    f = W.random_populations(1, 1, seed=7).reshape(9)
+    dphi = np.diag([3e-5, -2e-5])
+    out = O.collide_node(_node_params(1.0, 1.0, (2e-4, -1e-4)), f, dphi)
+    assert np.allclose(out["fstar"], out["feq"] + out["G"] + 0.5 * out["Fi"], atol=1e-16, rtol=0)
+
+
+def test_rlb_reduction_equal_times():
+    """tau2 = tau1 is the third-order RLB (Sec. III A): both odd and even
+    non-equilibrium orders relax with one factor."""
+    f = W.random_populations(1, 1, seed=9).reshape(9)
+    out = O.collide_node(_node_params(0.7, 0.7), f)
+    _, A2, A3 = O.projections(f, out["feq"])
+    _, B2, B3 = O.projections(out["fstar"], out["feq"])
+    k = 1 - 1 / 0.7
+    assert np.allclose(B2, k * A2, atol=1e-15)
+    assert np.allclose(B3[0, 0, 1], k * A3[0, 0, 1], atol=1e-15)
+
+
+# ------------------------------------------------------------ lattice steps
+
+def _lat(nx, ny, tau1, tau2, **kw):
+    return O.Lattice(O.Params(nx=nx, ny=ny, tau1=tau1, tau2=tau2, **{k: v for k, v in kw.items() if k != "mask"}),
+                     mask=kw.get("mask"))
+
+
+def test_uniform_flow_is_a_fixed_point():
+    """A uniform (rho, u) on a periodic lattice without force is invariant: f = f^eq
+    and G = 0, so eq2 returns f^eq, which streaming leaves unchanged."""
+    L = _lat(7, 5, 0.63, 1.1)
+    u = np.full((5, 7), 0.07), np.full((5, 7), -0.03)
+    L.init(*u, rho=np.full((5, 7), 1.02))
+    f0 = L.f.copy()
+    L.step(20)
+    assert np.abs(L.f - f0).max() < 1e-15
+
+
+def test_uniform_acceleration_is_exact():
+    """Uniform body force on a periodic lattice: rho stays, u(t) = u(0) + g t (eq11)."""
+    g = (1e-4, -3e-5)
+    L = _lat(6, 4, 0.9, 0.75, gx=g[0], gy=g[1])
+    L.init(np.full((4, 6), 0.01), np.full((4, 6), 0.02))
+    L.step(50)
+    rho, ux, uy = L.moments()
+    assert np.abs(rho - 1).max() < 1e-14
+    assert np.abs(ux - (0.01 + 50 * g[0])).max() < 1e-14
+    assert np.abs(uy - (0.02 + 50 * g[1])).max() < 1e-14
+
+
+def test_mass_conserved_with_walls_and_obstacles():
+    """Half-way bounce-back (eq_a20) and periodic streaming move populations without
+    loss, and the collision conserves mass: total mass is constant."""
+    nx, ny = 12, 9
+    mask = W.random_mask(nx, ny, seed=3, solid_frac=0.15)
+    L = _lat(nx, ny, 0.8, 1.3, periodic_x=True, periodic_y=False, gx=1e-5, mask=mask)
+    rho, ux, uy = W.random_fields(nx, ny, seed=4)
+    L.init(ux, uy, rho)
+    m0 = L.moments()[0].sum()
+    L.step(200)
+    assert abs(L.moments()[0].sum() - m0) < 1e-12 * m0
+
+
+def test_periodic_momentum_balance():
+    """Periodic lattice with force: total momentum sum(rho u) grows by sum(F) each step."""
+    nx, ny = 10, 8
+    g = (2e-5, 1e-5)
+    L = _lat(nx, ny, 0.7, 0.9, gx=g[0], gy=g[1])
+    rho, ux, uy = W.random_fields(nx, ny, seed=5)
+    L.init(ux, uy, rho)
+    r0, ux0, uy0 = L.moments()
+    L.step(30)
+    r1, ux1, uy1 = L.moments()
+    mass = r0.sum()
+    assert (r1 * ux1).sum() - (r0 * ux0).sum() == pytest.approx(30 * mass * g[0], abs=1e-13)
+    assert (r1 * uy1).sum() - (r0 * uy0).sum() == pytest.approx(30 * mass * g[1], abs=1e-13)
+
+
+# symmetry of the square lattice: rotation by 90 degrees and mirror x -> -x
+_ROT = [0, 2, 3, 4, 1, 6, 7, 8, 5]      # e_i rotated counter-clockwise is e_ROT[i]
+_MIR = [0, 3, 2, 1, 4, 6, 5, 8, 7]      # e_i with e_x negated is e_MIR[i]
+
+
+def _rotate_f(f):
+    n = f.shape[1]
+    out = np.empty_like(f)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for i in range(9):
+        out[_ROT[i], x, (-y) % n] = f[i, y, x]
+    return out
+
+
+def _rotate_scalar(a):
+    n = a.shape[0]
+    out = np.empty_like(a)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    out[x, (-y) % n] = a[y, x]
+    return out
+
+
+@pytest.mark.parametrize("g_mode", [O.G_LAGGED, O.G_CURRENT])
+def test_rotation_equivariance(g_mode):
+    """Every term of eq2 is built from tensors, so rotating the lattice state by 90
+    degrees commutes with a step (with the force and any obstacles rotated too)."""
+    n = 9
+    f = W.random_populations(n, n, seed=11, amp=0.3)
+    mask = W.random_mask(n, n, seed=12, solid_frac=0.12)
+    g = (3e-5, -1e-5)
+    A = _lat(n, n, 0.66, 1.4, gx=g[0], gy=g[1], g_mode=g_mode, mask=mask)
+    B = _lat(n, n, 0.66, 1.4, gx=-g[1], gy=g[0], g_mode=g_mode, mask=_rotate_scalar(mask))
+    A.set_f(f)
+    B.set_f(_rotate_f(f))
+    A.step(7)
+    B.step(7)
+    fa = _rotate_f(A.f)
+    fa[:, _rotate_scalar(mask) != 0] = 0.0
+    fb = B.f.copy()
+    fb[:, _rotate_scalar(mask) != 0] = 0.0
+    assert np.abs(fa - fb).max() < 1e-14
+
+
+def test_mirror_equivariance_with_walls():
+    """Mirroring x -> -x commutes with a step on a channel with walls in y."""
+    nx, ny = 8, 6
+    f = W.random_populations(nx, ny, seed=13)
+    A = _lat(nx, ny, 0.9, 0.6, periodic_y=False, gx=2e-5)
+    B = _lat(nx, ny, 0.9, 0.6, periodic_y=False, gx=-2e-5)
+    mir = lambda F: np.stack([F[_MIR[i]] for i in range(9)])[:, :, (-np.arange(nx)) % nx]
+    A.set_f(f)
+    B.set_f(mir(f))
+    A.step(9)
+    B.step(9)
+    assert np.abs(mir(A.f) - B.f).max() < 1e-14
+
+
+def test_lagged_and_current_agree_on_first_step():
+    """With Phi^{-1} := Phi^0 the lagged and current readings of eq_Gi give the
+    same first step."""
+    n = 8
+    _, ux, uy = W.random_fields(n, n, seed=21, u_amp=0.1)
+    A = _lat(n, n, 0.6, 0.8, g_mode=O.G_LAGGED).init(ux, uy)
+    B = _lat(n, n, 0.6, 0.8, g_mode=O.G_CURRENT).init(ux, uy)
+    A.step(1)
+    B.step(1)
+    assert np.abs(A.f - B.f).max() < 1e-17
+    A.step(1)
+    B.step(1)
+    assert np.abs(A.f - B.f).max() > 0  # they part afterwards
+
+
+# -------------------------------------------- closed forms of Secs. II D, III
+
+def _poiseuille_exact(ny, tau1, magic, u_c):
+    """eq_a3 with y_j = j - 1/2 (j = 1..N) plus the slip of eq_a28."""
+    nu = P.nu_from_tau(tau1)
+    g = P.poiseuille_acceleration(u_c, nu, ny)
+    tau2 = P.tau2_from_magic(tau1, magic)
+    us = (16 * tau1 * tau2 - 8 * tau1 - 8 * tau2 + 1) / (4 * (2 * tau1 - 1)) * g
+    y = np.arange(1, ny + 1) - 0.5
+    return 4 * u_c / ny ** 2 * y * (ny - y) + us, us, g
+
+
+@pytest.mark.parametrize("tau1,magic", [(0.6, 1 / 12), (0.6, 3 / 16), (1.0, 1 / 4), (5.0, 1 / 2), (1.0, 3 / 16)])
+def test_poiseuille_closed_form(tau1, magic):
+    """The steady discrete Poiseuille profile with half-way bounce-back is the
+    parabola of eq_a3 shifted by the slip of eq_a28 (zero at Lambda = 3/16)."""
+    ny, u_c = 16, 0.01
+    exact, us, g = _poiseuille_exact(ny, tau1, magic, u_c)
+    pr = W.poiseuille(ny, tau1, magic, nx=1, u_c=u_c, profile=exact)
+    L = _lat(1, ny, pr.tau_s, pr.tau_s2, periodic_x=True, periodic_y=False, gx=pr.g[0])
+    L.init(pr.ux, pr.uy)
+    L.step(20000)
+    _, ux, uy = L.moments()
+    assert np.abs(ux[:, 0] - exact).max() < 1e-10 * u_c
+    assert np.abs(uy).max() < 1e-10 * u_c
+    if magic == 3 / 16:
+        assert abs(us) < 1e-18
+
+
+def test_poiseuille_slip_depends_on_magic_only():
+    """u_s / u_c = (16 Lambda - 3) / (3 N^2) for any tau1 (eq_a28 with eq_a29)."""
+    ny, u_c, magic = 12, 0.01, 0.5
+    slips = []
+    for tau1 in (0.6, 2.0):
+        exact, us, _ = _poiseuille_exact(ny, tau1, magic, u_c)
+        pr = W.poiseuille(ny, tau1, magic, nx=1, u_c=u_c, profile=exact - us)
+        L = _lat(1, ny, pr.tau_s, pr.tau_s2, periodic_y=False, gx=pr.g[0]).init(pr.ux, pr.uy)
+        L.step(60000 if tau1 < 1 else 20000)
+        _, ux, _ = L.moments()
+        y = np.arange(1, ny + 1) - 0.5
+        slips.append((ux[:, 0] - 4 * u_c / ny ** 2 * y * (ny - y)).mean())
+    for s in slips:
+        assert s / u_c == pytest.approx((16 * magic - 3) / (3 * ny ** 2), rel=1e-6)
+
+
+def test_rlb_poiseuille_slips():
+    """With tau2 = tau1 (RLB) the slip of eq_a28 does not vanish (Fig. test3_fig2)."""
+    ny, u_c, tau1 = 16, 0.01, 1.2
+    magic = (tau1 - 0.5) ** 2
+    exact, us, g = _poiseuille_exact(ny, tau1, magic, u_c)
+    assert abs(us) > 1e-3 * u_c
+    pr = W.poiseuille(ny, tau1, magic, nx=1, u_c=u_c, profile=exact)
+    assert pr.tau_s2 == pytest.approx(tau1)
+    L = _lat(1, ny, pr.tau_s, pr.tau_s2, periodic_y=False, gx=pr.g[0]).init(pr.ux, pr.uy)
+    L.step(20000)
+    assert np.abs(L.moments()[1][:, 0] - exact).max() < 1e-10 * u_c
+
+
+def test_poiseuille_wall_force_balances_body_force():
+    """At steady state the momentum exchanged with the walls (Sec. III D) equals the
+    total body force on the fluid."""
+    ny, u_c, tau1, magic = 10, 0.01, 0.8, 3 / 16
+    exact, _, g = _poiseuille_exact(ny, tau1, magic, u_c)
+    pr = W.poiseuille(ny, tau1, magic, nx=4, u_c=u_c, profile=exact)
+    L = _lat(4, ny, pr.tau_s, pr.tau_s2, periodic_y=False, gx=g).init(pr.ux, pr.uy)
+    L.step(5000)
+    rho = L.moments()[0]
+    Fx, Fy = L.drag()
+    assert Fx == pytest.approx(rho.sum() * g, rel=1e-9)
+    assert abs(Fy) < 1e-14
+
+
+def test_couette_flow_with_moving_wall():
+    """Plane Couette flow between a stationary half-way wall and a moving wall
+    (inlet-class nodes): the steady profile is linear, u(y_j) = U (j + 1/2) / H,
+    H = ny - 1 (bottom wall at y = -1/2, moving wall at y = ny - 3/2)."""
+    nx, ny, U = 2, 12, 0.02
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[ny - 1, :] = O.INLET
+    H = ny - 1
+    y = np.arange(ny - 1) + 0.5
+    prof = np.zeros((ny, nx))
+    prof[:ny - 1] = (U * y / H)[:, None]
+    L = _lat(nx, ny, 0.9, P.tau2_from_magic(0.9, 3 / 16), periodic_y=False, wall_ux=U, mask=mask)
+    L.init(prof * 0.5, np.zeros((ny, nx)))
+    L.step(30000)
+    _, ux, uy = L.moments()
+    assert np.abs(ux[:ny - 1, 0] - U * y / H).max() < 1e-10 * U
+    assert np.abs(uy).max() < 1e-12
+
+
+def test_uniform_flow_through_inlet_and_outlet():
+    """A uniform stream entering through a moving-wall inlet at its own speed and
+    leaving through the zero-gradient outlet is an exact steady state."""
+    nx, ny, U = 10, 4, 0.03
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[:, 0] = O.INLET
+    mask[:, nx - 1] = O.OUTLET
+    L = _lat(nx, ny, 0.7, 0.8, periodic_x=False, periodic_y=True, wall_ux=U, mask=mask)
+    ux = np.full((ny, nx), U)
+    L.init(ux, np.zeros((ny, nx)))
+    f0 = L.f.copy()
+    L.step(40)
+    fluid = mask == O.FLUID
+    assert np.abs(L.f[:, fluid] - f0[:, fluid]).max() < 1e-15
+
+
+def test_taylor_green_decay_rate():
+    """Sec. III B: the Taylor-Green velocity amplitude decays as exp(-2 nu k^2 t),
+    nu = (tau1 - 1/2)/3 (eq_mu); the viscosity fitted over 1000 steps on 64^2 agrees
+    to 1% (the error is O(dx^2) + O(Ma^2), Sec. III B)."""
+    pr = W.taylor_green(64, u0=0.04, re=100.0, magic=0.25)
+    L = _lat(64, 64, pr.tau_s, pr.tau_s2).init(pr.ux, pr.uy, pr.rho)
+    L.step(1000)
+    _, ux, uy = L.moments()
+    mode_x = pr.ux / pr.meta["u0"]
+    amp = (ux * mode_x).sum() / (mode_x * mode_x).sum()
+    nu = pr.meta["nu"]
+    k = pr.meta["k"]
+    nu_fit = -math.log(amp / pr.meta["u0"]) / (2 * k * k * 1000)
+    assert nu_fit / nu - 1 == pytest.approx(0.0, abs=0.01)
+    # kinetic energy decays at twice the rate
+    ke = (ux ** 2 + uy ** 2).sum() / (pr.ux ** 2 + pr.uy ** 2).sum()
+    assert -math.log(ke) / (4 * k * k * 1000) / nu - 1 == pytest.approx(0.0, abs=0.01)
+
+
+def test_l2_norm_definition():
+    """eq_n1 on a hand example: sqrt(((1-1)^2 + (2-4)^2) / (1 + 16))."""
+    assert O.l2(np.array([1.0, 2.0]), np.array([1.0, 4.0])) == pytest.approx(math.sqrt(4 / 17), abs=1e-16)
