@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused D2Q9 TRT-RLB step on GB300.
+
+Default workload: the double shear layer (Sec. III A) on three 1024 x 1024
+periodic lattices, Re = 1e4, 1e5, 1e7 (kappa = 80, delta = 0.05, u_c = 0.04,
+tau_{s,2} = 0.625), FP32 storage, lagged G.  One benchmark step is one time
+step of all three lattices.  The L2 cache is flushed (512 MiB memset) before
+every timed step; each step is timed with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the same workload on the host
+cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 TRT-RLB MLUPS & % HBM roofline; served solves/s, p50/p99 latency"
+UNIT = "MLUPS"
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+PHI_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4}
+
+
+def workload(name: str):
+    """(problems, storage, description) of a named workload."""
+    from paper_2312_10318_gb300 import workloads as W
+    if name == "dsl1024":
+        res = (1e4, 1e5, 1e7)
+        probs = [W.double_shear_layer(1024, re=r) for r in res]
+        desc = ("double shear layer, 3 lattices 1024x1024 periodic (Re 1e4, 1e5, 1e7), kappa=80, "
+                "delta=0.05, u_c=0.04, tau_s2=0.625, FP32 storage, G lagged")
+        return probs, "f32", desc
+    if name == "dsl4096":
+        probs = [W.double_shear_layer(4096, re=1e5)]
+        return probs, "f32", "double shear layer, 1 lattice 4096x4096 periodic, Re 1e5, FP32 storage, G lagged"
+    if name == "dsl4096_f16":
+        probs = [W.double_shear_layer(4096, re=1e5)]
+        return probs, "f16", "double shear layer, 1 lattice 4096x4096 periodic, Re 1e5, FP16-shifted storage, G lagged"
+    if name == "tg64":
+        probs = [W.taylor_green(64, 0.04, 100.0, magic=0.25)]
+        return probs, "f64", "Taylor-Green 64x64 periodic, u0=0.04, Re=100, magic 1/4, FP64"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
+    """Algorithmic bytes of one node update: 9 populations read and written, plus
+    (lagged G) two Phi values read and two written."""
+    b = 2 * 9 * STORAGE_BYTES[storage]
+    if g_mode == "lagged":
+        b += 4 * PHI_BYTES[storage]
+    return b
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2312_10318_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    pat = re.compile(r"^traffic_per_launch_bytes\[(\w+)\]:\s*([0-9.eE+]+)\s+source_hash:\s*(\w+)")
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(p):
+            m = pat.match(line.strip())
+            if m and m.group(1) == workload_name and m.group(3) == kernel_source_hash():
+                return float(m.group(2))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(problems, seconds: float = 12.0):
+    """The FP64 CPU oracle on a bounded sample of the workload: as many time steps
+    of the first lattice as fit in about `seconds`."""
+    import oracle as O
+    pr = problems[0]
+    lat = O.Lattice(O.Params(nx=pr.nx, ny=pr.ny, tau1=pr.tau_s, tau2=pr.tau_s2,
+                             periodic_x=pr.periodic[0], periodic_y=pr.periodic[1],
+                             gx=pr.g[0], gy=pr.g[1], wall_ux=pr.wall_u[0], wall_uy=pr.wall_u[1],
+                             wall_rho=pr.wall_rho), mask=pr.mask)
+    lat.init(pr.ux, pr.uy, pr.rho)
+    lat.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        lat.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": pr.nodes * n / dt / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} time steps of one {pr.nx}x{pr.ny} lattice ({pr.name}) of the workload, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, problems, desc, budget_s: float = 60.0):
+    """The FP64 CPU oracle on the workload, on the host cores (rank 0 only).  Each
+    step advances every lattice of the workload by one time step on a strip of
+    its rows (periodic in y with the strip's height), sized so the whole run takes
+    about `budget_s`; MLUPS counts the nodes actually updated."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    def make(pr, rows):
+        lat = O.Lattice(O.Params(nx=pr.nx, ny=rows, tau1=pr.tau_s, tau2=pr.tau_s2,
+                                 periodic_x=pr.periodic[0], periodic_y=pr.periodic[1] or rows < pr.ny,
+                                 gx=pr.g[0], gy=pr.g[1], wall_ux=pr.wall_u[0], wall_uy=pr.wall_u[1],
+                                 wall_rho=pr.wall_rho),
+                        mask=None if pr.mask is None else pr.mask[:rows])
+        rho = None if pr.rho is None else pr.rho[:rows]
+        return lat.init(pr.ux[:rows], pr.uy[:rows], rho)
+
+    probe = make(problems[0], problems[0].ny)
+    t0 = time.perf_counter()
+    probe.step(1)
+    full = (time.perf_counter() - t0) * len(problems)
+    frac = min(1.0, budget_s / max(1e-9, (args.steps + args.warmup) * full))
+    lats = []
+    for pr in problems:
+        rows = max(8, min(pr.ny, int(pr.ny * frac) // 8 * 8))
+        lats.append(make(pr, rows))
+    for _ in range(args.warmup):
+        for lat in lats:
+            lat.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for lat in lats:
+            lat.step(1)
+    dt = time.perf_counter() - t0
+    nodes = sum(l.p.nx * l.p.ny for l in lats)
+    value = nodes * args.steps / dt / 1e6
+    sample = (f"each step: one time step of {len(lats)} lattice(s) on {lats[0].p.nx}x{lats[0].p.ny} "
+              f"row strips of the workload")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "nodes_per_step": nodes, "implementation": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dsl1024")
+    ap.add_argument("--flush-mib", type=int, default=512)
+    ap.add_argument("--e2e-steps", type=int, default=100, help="time steps per end-to-end solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    problems, storage, desc = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, problems, desc)
+
+    import numpy as np
+    import torch
+    from paper_2312_10318_gb300 import Lattice
+
+    world, rank, local = dist_setup()
+    if args.gpus != world:
+        raise SystemExit(f"--gpus {args.gpus} needs torchrun with {args.gpus} processes (WORLD_SIZE={world})")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    lats = []
+    for pr in problems:
+        lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode="lagged", stream=stream,
+                      **pr.lattice_kwargs())
+        lat.init(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
+                   for a in (pr.ux, pr.uy, pr.rho)))
+        lats.append(lat)
+    nodes = sum(p.nodes for p in problems)
+    flush = torch.empty(args.flush_mib << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        for lat in lats:
+            lat.step(1)
+    barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    events = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for lat in lats:
+            lat.step(1)
+        e1.record(stream)
+        events.append((e0, e1))
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    clk = clocks.stop() if clocks else None
+    local_ms = sum(step_ms)
+    total_ms = local_ms
+    if dist is not None:
+        t = torch.tensor([local_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nodes * args.steps * world / (total_ms / 1e3) / 1e6
+
+    # roofline of the step kernel: algorithmic bytes per launch / mean launch time
+    launches = args.steps * len(lats)
+    launch_s = local_ms / 1e3 / launches
+    per_launch_bytes = bytes_per_node(storage) * nodes / len(lats)
+    achieved = per_launch_bytes / launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = recorded_traffic(args.workload)
+
+    # end to end through the C ABI with pinned host buffers: init from host
+    # fields, e2e_steps time steps, macroscopic fields back to host
+    host_in = [[torch.from_numpy(np.ascontiguousarray(a if a is not None else np.ones((p.ny, p.nx)))).pin_memory()
+                for a in (p.ux, p.uy, p.rho)] for p in problems]
+    host_out = [[torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(3)] for p in problems]
+    e2e_times = []
+    for rep in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        for lat, (ux, uy, rho) in zip(lats, host_in):
+            lat.init(ux, uy, rho)
+        for lat in lats:
+            lat.step(args.e2e_steps)
+        for lat, out in zip(lats, host_out):
+            lat.moments(*out)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = statistics.median(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = nodes * args.e2e_steps * world / e2e_t / 1e6
+    field_bytes = 3 * 8 * nodes
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+            "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
+                       "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
+                       "g_mode": "lagged", "parallelism": f"replicas x{world}",
+                       "l2": f"{args.flush_mib} MiB memset before every timed step (outside the events)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": None if traffic is None else traffic,
+                         "kernel": "trt::k_step (fused AA stream-collide)",
+                         "algorithmic_bytes_per_node": bytes_per_node(storage),
+                         "launch_ms": launch_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": field_bytes / args.e2e_steps,
+                    "d2h_bytes_per_step": field_bytes / args.e2e_steps,
+                    "solve": f"init from pinned host fields + {args.e2e_steps} steps + fields to host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(problems)
+        print(json.dumps(line), flush=True)
+    for lat in lats:
+        lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * trtrlb — GB300-native D2Q9 two-relaxation-time regularized lattice
+ * Boltzmann (TRT-RLB) library: the C ABI.
+ *
+ * The scheme is the one of Yu, Qin, Chen, Shu and Yuan (arXiv 2312.10318).
+ * Equation names below are that paper's equation labels (eq2, eq4, eq6, eq9,
+ * eq11, eq_Gi, eq_a20, eq_a29, eq_mu ...).  One time step is eq2: collide with
+ * the regularized TRT operator, add the cubic-error compensation G_i (eq_Gi)
+ * and the forcing term F_i (eq6), stream, and apply half-way bounce-back
+ * (eq_a20) at walls.
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice units: dx = dt = c = 1, c_s^2 = 1/3.
+ *   - A field is nx*ny values, index y*nx + x (x fastest).  Populations are
+ *     9*nx*ny values, index (i*ny + y)*nx + x, with the paper's D2Q9 numbering
+ *     e_0..e_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ *   - Pointers to fields may be host or device memory (detected per call).
+ *     The caller owns them; the library copies in and out.
+ *   - Every call is asynchronous on the handle's stream, except where a call
+ *     writes into host memory: that call synchronises the stream before it
+ *     returns.
+ *   - Return value: TRTRLB_OK (0) or a negative TRTRLB_E* code; on error the
+ *     handle is left as it was, and trtrlb_last_error() describes the cause.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef TRTRLB_H
+#define TRTRLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define TRTRLB_OK 0
+#define TRTRLB_EINVAL (-1)    /* invalid argument or parameter combination      */
+#define TRTRLB_ENOMEM (-2)    /* device or host allocation failed               */
+#define TRTRLB_ECUDA (-3)     /* a CUDA runtime call failed                     */
+#define TRTRLB_EUNSTABLE (-4) /* diagnostics found NaN/Inf or |u| beyond bound   */
+#define TRTRLB_ETIMEOUT (-5)  /* a bounded wait gave up                         */
+#define TRTRLB_ENOTSUP (-6)   /* combination not built into this library        */
+
+/* Population storage formats.  All collision arithmetic of the reduced
+ * formats runs in FP32 on the shifted deviation f_i - w_i rho0; FP64 storage
+ * runs FP64 arithmetic. */
+#define TRTRLB_F64 0
+#define TRTRLB_F32 1
+#define TRTRLB_F16_SHIFTED 2
+#define TRTRLB_BF16_SHIFTED 3
+
+/* Time level of Phi_abg = rho u_a^3 delta... in the compensation term G_i
+ * (eq_Gi).  The paper does not say which level; d_gamma Phi is a central
+ * difference over neighbouring nodes.
+ *   LAGGED : Phi from the previous step (Phi^{-1} := Phi^0), used by the
+ *            in-place AA kernel, which cannot see neighbours' current moments.
+ *   CURRENT: Phi of the current step (two-pass reference semantics).
+ *   OFF    : G_i = 0. */
+#define TRTRLB_G_LAGGED 0
+#define TRTRLB_G_CURRENT 1
+#define TRTRLB_G_OFF 2
+
+/* Boundary mask classes (one byte per node). */
+#define TRTRLB_FLUID 0
+#define TRTRLB_SOLID 1  /* stationary wall node: half-way bounce-back, eq_a20 */
+#define TRTRLB_INLET 2  /* moving wall node (velocity inlet): bounce-back with
+                           the correction -2 w_i rho_w (e_i.u_w)/c_s^2      */
+#define TRTRLB_OUTLET 3 /* zero-gradient outlet ghost: does not collide and
+                           re-emits the post-collision populations of its
+                           inward neighbour (x-1, y), which must be fluid    */
+
+/* Problem statement (Sec. II B, eq2; eq_mu; eq_a2; eq_a29). */
+typedef struct {
+    int32_t nx, ny;          /* lattice size: 1 <= ny <= 131070, 1 <= nx <= 2^24,
+                                (nx + 63) * ny <= 2^30                           */
+    int32_t periodic_x;      /* 1: periodic in x; 0: stationary half-way walls   */
+    int32_t periodic_y;      /*    just outside x = -1/2 and x = nx - 1/2 (y alike) */
+    double tau_s;            /* tau_{s,1} > 1/2: relaxes the 1st and 2nd order;
+                                kinematic viscosity nu = (tau_s - 1/2)/3 (eq_mu) */
+    double tau_s2;           /* tau_{s,2} > 1/2: relaxes the 3rd order, or NaN   */
+    double magic;            /* Lambda_s = (tau_s - 1/2)(tau_s2 - 1/2) (eq_a29),
+                                or NaN.  Exactly one of tau_s2 / magic may be NaN;
+                                if both are given they must agree to 1e-12 rel. */
+    double gx, gy;           /* body acceleration; F = rho g (eq_a2)             */
+    double rho0;             /* reference density of the shifted storage (> 0)   */
+    double wall_ux, wall_uy; /* velocity of TRTRLB_INLET nodes                   */
+    double wall_rho;         /* density rho_w in the moving-wall correction      */
+    int32_t storage;         /* TRTRLB_F64 | F32 | F16_SHIFTED | BF16_SHIFTED    */
+    int32_t g_mode;          /* TRTRLB_G_LAGGED | G_CURRENT | G_OFF              */
+} trtrlb_params;
+
+typedef struct trtrlb_lattice* trtrlb_t;
+
+/* Fills *p with defaults: periodic 64x64, tau_s = 0.8, magic = 1/4 (tau_s2 NaN),
+ * no force, rho0 = wall_rho = 1, FP32 storage, LAGGED. */
+void trtrlb_default_params(trtrlb_params* p);
+
+/* Creates a lattice and allocates its device memory on the current device.
+ *   mask   : NULL (all fluid) or nx*ny bytes of TRTRLB_* classes, host memory;
+ *   stream : cudaStream_t all work of the handle is ordered on (NULL = legacy
+ *            default stream);
+ *   out    : receives the handle; unchanged on error.
+ * The populations start at rest with density rho0.  Errors: EINVAL (bad size,
+ * tau, magic/tau_s2, storage, mask class, outlet without a fluid inward
+ * neighbour), ENOTSUP (G_CURRENT with the in-place kernel), ENOMEM, ECUDA. */
+int trtrlb_create(const trtrlb_params* p, const uint8_t* mask, void* stream, trtrlb_t* out);
+
+/* Frees all memory of the handle (synchronises its stream).  NULL is a no-op. */
+int trtrlb_destroy(trtrlb_t h);
+
+/* Changes the stream later work is ordered on. */
+int trtrlb_set_stream(trtrlb_t h, void* stream);
+
+/* Initial state from macroscopic fields (t = 0):
+ *   f_i = f_i^eq(rho, u) - (1/2) w_i e_i.F / c_s^2   (eq4, eq11),
+ * and Phi of the previous level := Phi of (rho, u).  rho may be NULL (rho0
+ * everywhere); ux, uy are required.  Values at non-fluid nodes are ignored. */
+int trtrlb_init(trtrlb_t h, const double* rho, const double* ux, const double* uy);
+
+/* Advances nsteps >= 0 time steps of eq2 (asynchronous). */
+int trtrlb_step(trtrlb_t h, int64_t nsteps);
+
+/* Macroscopic fields of the current state (eq11): rho = sum f_i and
+ * u = (sum e_i f_i)/rho + g/2, FP64.  Any pointer may be NULL.  Non-fluid
+ * nodes report 0. */
+int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy);
+
+/* Populations f_i(x, t) of the current state as 9*nx*ny FP64 values, and
+ * optionally (phi != NULL) the previous-level Phi as 2*nx*ny values
+ * (Phi_xxx then Phi_yyy).  Non-fluid nodes report 0 populations. */
+int trtrlb_get_f(trtrlb_t h, double* f, double* phi);
+
+/* Replaces the populations of the current state (9*nx*ny FP64 values, rounded
+ * to the storage format).  phi == NULL: the previous-level Phi becomes that of
+ * the new state; otherwise 2*nx*ny values are taken as given.  Values at
+ * non-fluid nodes are ignored. */
+int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi);
+
+/* Number of steps taken since the last init / set_f. */
+int64_t trtrlb_time(trtrlb_t h);
+
+/* FP64 diagnostics over the fluid nodes of the current state (deterministic
+ * fixed-order reduction).  out[8] receives:
+ *   [0] total mass sum rho, [1] sum rho u_x, [2] sum rho u_y,
+ *   [3] kinetic energy sum rho |u|^2 / 2, [4] max |u|,
+ *   [5] number of nodes whose populations are not finite,
+ *   [6], [7] momentum-exchange force on the walls (Sec. III D) x, y:
+ *   the sum over links from fluid nodes into solid nodes or across
+ *   non-periodic edges of 2 e_i f_ibar(x_f, t).
+ * out may be host or device memory. */
+int trtrlb_diagnostics(trtrlb_t h, double* out);
+
+/* Device bytes held by the handle. */
+int64_t trtrlb_device_bytes(trtrlb_t h);
+
+/* Static description of an error code. */
+const char* trtrlb_strerror(int code);
+
+/* Message of the last error on this handle ("" if none); NULL handle: the
+ * last error of a failed trtrlb_create on this thread. */
+const char* trtrlb_last_error(trtrlb_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRTRLB_H */

@@ -84,6 +84,7 @@ def lib():
         L.orc_l2.argtypes = [_D, _D, C.c_int64]
         L.orc_l2.restype = C.c_double
         L.orc_drag.argtypes = [P, vp, _D, _D]
+        L.orc_num_threads.restype = C.c_int
         _LIB = L
     return _LIB
 
@@ -230,6 +231,11 @@ def l2(qn, qa) -> float:
     return lib().orc_l2(a, b, a.size)
 
 
+def num_threads() -> int:
+    """OpenMP threads of the oracle's collision loop."""
+    return int(lib().orc_num_threads())
+
+
 def tau2_from_magic(tau1: float, magic: float) -> float:
     """tau_{s,2} from Lambda_s = (tau1 - 1/2)(tau2 - 1/2), eq_a29."""
     return 0.5 + magic / (tau1 - 0.5)
@@ -241,5 +247,5 @@ def viscosity(tau1: float) -> float:
 
 
 __all__ = ["Params", "Lattice", "lattice", "hermite", "equilibrium", "forcing", "compensation",
-           "projections", "macroscopic", "collide_node", "l2", "tau2_from_magic", "viscosity",
+           "projections", "macroscopic", "collide_node", "l2", "num_threads", "tau2_from_magic", "viscosity",
            "FLUID", "SOLID", "INLET", "OUTLET", "G_LAGGED", "G_CURRENT", "G_OFF"]

@@ -44,6 +44,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define NQ 9
 #define ND 2
@@ -89,6 +92,15 @@ static int opposite(int i) {
     for (int j = 0; j < NQ; ++j)
         if (EV[j][0] == -EV[i][0] && EV[j][1] == -EV[i][1]) return j;
     return -1;
+}
+
+/* Threads the collision loop runs on. */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ---- exported lattice description, for the identity tests ------------- */

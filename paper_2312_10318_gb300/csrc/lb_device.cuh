@@ -1,0 +1,320 @@
+// Device side of the D2Q9 TRT-RLB library: lattice constants, the per-node
+// collision (eq2 with eq4, eq6, eq9, eq11, eq_Gi) in D2Q9-reduced form, and the
+// AA-pattern storage rules shared by every kernel.
+//
+// Storage.  Populations live in one array F[9][ny][pitch] (x fastest, pitch a
+// multiple of 64 elements) as the shifted deviation d_i = f_i - w_i rho0 in
+// the storage type S.  The AA pattern keeps one copy: for a state at an EVEN
+// time level, f_i(x) sits at F[i][x]; at an ODD level it sits at
+// F[ibar][x - e_i] when x - e_i is a streaming node (fluid or outlet ghost
+// inside the domain), and at F[i][x] when x - e_i is a wall (bounce-back
+// storage).  An even step reads and writes only a node's own slots (it writes
+// f*_i to F[ibar][x]); an odd step reads the neighbour slots above and writes
+// f*_i to F[i][x + e_i] (or F[ibar][x] at a wall), which are the same nine
+// locations, so the update is in place and race-free.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace trt {
+
+// ---- D2Q9 (Sec. II B) -----------------------------------------------------
+__host__ __device__ constexpr int ex(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+}
+__host__ __device__ constexpr double wgt(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+enum : uint8_t { FLUID = 0, SOLID = 1, INLET = 2, OUTLET = 3 };
+enum : int { K_STREAM = 0, K_WALL = 1, K_MOVING = 2 };
+enum : int { G_LAGGED = 0, G_CURRENT = 1, G_OFF = 2 };
+
+// ---- storage formats --------------------------------------------------------
+template <typename S> struct Fmt;
+template <> struct Fmt<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(double v) { return v; }
+    static __device__ __forceinline__ double st(double v) { return v; }
+};
+template <> struct Fmt<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(float v) { return v; }
+    static __device__ __forceinline__ float st(float v) { return v; }
+};
+template <> struct Fmt<__half> {
+    using C = float;
+    static __device__ __forceinline__ float ld(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half st(float v) { return __float2half_rn(v); }
+};
+template <> struct Fmt<__nv_bfloat16> {
+    using C = float;
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---- kernel arguments -------------------------------------------------------
+template <typename C> struct Args {
+    void* f;              // S[9][ny][pitch]
+    const C* phi_in;      // [2][ny][pitch]: Phi of the previous level
+    C* phi_out;           // [2][ny][pitch]: Phi of this level
+    const uint8_t* mask;  // [ny][pitch] or nullptr
+    int nx, ny, pitch;
+    long long plane;      // ny * pitch
+    int px, py;           // periodic flags
+    C k1, k2, kf;         // 1 - 1/tau1, 1 - 1/tau2, 1 - 1/(2 tau1)
+    C gx, gy, rho0;
+    C corr[9];            // moving-wall term 2 w_i rho_w (e_i.u_w) / c_s^2
+};
+
+// Neighbourhood of node (x, y): wrapped coordinates and out-of-domain flags.
+struct Nbh {
+    int xm, xp, ym, yp;
+    bool oxm, oxp, oym, oyp;
+};
+
+template <typename C>
+__device__ __forceinline__ Nbh neighbours(const Args<C>& a, int x, int y) {
+    Nbh n;
+    n.xm = x - 1; n.xp = x + 1; n.ym = y - 1; n.yp = y + 1;
+    n.oxm = n.oxp = n.oym = n.oyp = false;
+    if (n.xm < 0) { if (a.px) n.xm += a.nx; else n.oxm = true; }
+    if (n.xp >= a.nx) { if (a.px) n.xp -= a.nx; else n.oxp = true; }
+    if (n.ym < 0) { if (a.py) n.ym += a.ny; else n.oym = true; }
+    if (n.yp >= a.ny) { if (a.py) n.yp -= a.ny; else n.oyp = true; }
+    return n;
+}
+
+// Linear index (within a plane) of x + e_i and whether it lies outside.
+template <int I>
+__device__ __forceinline__ long long nb_index(const Nbh& n, int x, int y, int pitch, bool& out) {
+    constexpr int dx = ex(I), dy = ey(I);
+    const int cx = dx > 0 ? n.xp : (dx < 0 ? n.xm : x);
+    const int cy = dy > 0 ? n.yp : (dy < 0 ? n.ym : y);
+    out = (dx > 0 && n.oxp) || (dx < 0 && n.oxm) || (dy > 0 && n.oyp) || (dy < 0 && n.oym);
+    return (long long)cy * pitch + cx;
+}
+
+__device__ __forceinline__ int kind_of(uint8_t c) {
+    return c == SOLID ? K_WALL : (c == INLET ? K_MOVING : K_STREAM);
+}
+
+// Link kinds of the 8 neighbours x + e_i (index 0 unused) and their indices.
+template <bool GENERAL, typename C>
+__device__ __forceinline__ void links(const Args<C>& a, int x, int y, long long (&nb)[9],
+                                      int (&kind)[9]) {
+    const Nbh n = neighbours(a, x, y);
+    bool out[9];
+    nb[0] = (long long)y * a.pitch + x;
+    kind[0] = K_STREAM;
+    out[0] = false;
+#define TRT_NB(I) nb[I] = nb_index<I>(n, x, y, a.pitch, out[I]);
+    TRT_NB(1) TRT_NB(2) TRT_NB(3) TRT_NB(4) TRT_NB(5) TRT_NB(6) TRT_NB(7) TRT_NB(8)
+#undef TRT_NB
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (!GENERAL) {
+            kind[i] = K_STREAM;
+        } else if (out[i]) {
+            kind[i] = K_WALL;
+        } else {
+            kind[i] = a.mask ? kind_of(a.mask[nb[i]]) : K_STREAM;
+        }
+    }
+}
+
+// Location (offset into F) of f_i(x, t) for a state whose level has parity ODD.
+template <bool ODD>
+__device__ __forceinline__ long long pop_loc(long long plane, const long long (&nb)[9],
+                                             const int (&kind)[9], int i) {
+    if (!ODD) return (long long)i * plane + nb[0];
+    const int j = opp(i);  // x - e_i = x + e_j
+    return kind[j] == K_STREAM ? (long long)j * plane + nb[j] : (long long)i * plane + nb[0];
+}
+
+// ---- the collision ----------------------------------------------------------
+// d: shifted pre-collision populations d_i = f_i - w_i rho0 of one node.
+// dpx = d_x Phi_xxx, dpy = d_y Phi_yyy (central differences, already halved).
+// o: shifted post-collision populations f*_i - w_i rho0, the right-hand side
+// of eq2.  In D2Q9 every Hermite contraction collapses: with
+//   a1 = j + F,
+//   a2_ab = rho u_a u_b + (1 - 1/tau1) A_ab + (1 - 1/(2 tau1))(F_a u_b + u_a F_b)
+//           - (1 - 1/(2 tau1)) d_g Phi_abg,
+//   a3_xxy = rho u_x^2 u_y + (1 - 1/tau2) A_xxy  (and xyy alike),
+// f*_i = w_i [rho + 3 e_i.a1 + 9/2 H_i,ab a2_ab + 27/2 (H_i,xxy a3_xxy +
+// H_i,xyy a3_xyy)], because 1/(2 c_s^4) = 1/(6 c_s^6) = 9/2, H_xxx = H_yyy = 0
+// and the first-order terms of eq2 combine into w_i e_i.(j + F)/c_s^2.
+// Returns rho and u (eq11, with the half-force shift).
+template <typename C>
+__device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k2,
+                                        const C kf, const C gx, const C gy, const C rho0,
+                                        C (&o)[9], C& rho_o, C& ux_o, C& uy_o) {
+    const C third = C(1) / C(3);
+    const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const C jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const C sxx = (d[1] + d[3]) + (d[5] + d[6]) + (d[7] + d[8]);
+    const C syy = (d[2] + d[4]) + (d[5] + d[6]) + (d[7] + d[8]);
+    const C pxy = (d[5] + d[7]) - (d[6] + d[8]);
+    const C qxxy = (d[5] + d[6]) - (d[7] + d[8]);
+    const C qxyy = (d[5] + d[8]) - (d[6] + d[7]);
+    const C rho = rho0 + drho;
+    const C inv = C(1) / rho;
+    const C ux = jx * inv + C(0.5) * gx;
+    const C uy = jy * inv + C(0.5) * gy;
+    const C Fx = rho * gx, Fy = rho * gy;
+    const C rux = rho * ux, ruy = rho * uy;
+    const C ruxx = rux * ux, ruyy = ruy * uy, ruxy = rux * uy;
+    // eq9 with the equilibrium moments of eq9_2 (A_x = -F_x/2 is folded into a1)
+    const C Axx = sxx - third * drho - ruxx;
+    const C Ayy = syy - third * drho - ruyy;
+    const C Axy = pxy - ruxy;
+    const C Axxy = qxxy - third * jy - ruxx * uy;
+    const C Axyy = qxyy - third * jx - ruyy * ux;
+    const C a1x = jx + Fx, a1y = jy + Fy;
+    const C a2xx = ruxx + k1 * Axx + kf * (C(2) * Fx * ux - dpx);
+    const C a2yy = ruyy + k1 * Ayy + kf * (C(2) * Fy * uy - dpy);
+    const C a2xy = ruxy + k1 * Axy + kf * (Fx * uy + ux * Fy);
+    const C a3xxy = ruxx * uy + k2 * Axxy;
+    const C a3xyy = ruyy * ux + k2 * Axyy;
+    const C c13 = drho + C(3) * a2xx - C(1.5) * a2yy;
+    const C o13 = C(3) * a1x - C(4.5) * a3xyy;
+    const C c24 = drho - C(1.5) * a2xx + C(3) * a2yy;
+    const C o24 = C(3) * a1y - C(4.5) * a3xxy;
+    const C cd = drho + C(3) * (a2xx + a2yy);
+    const C c57 = cd + C(9) * a2xy, c68 = cd - C(9) * a2xy;
+    const C o57 = C(3) * (a1x + a1y) + C(9) * (a3xxy + a3xyy);
+    const C o68 = C(3) * (a1y - a1x) + C(9) * (a3xxy - a3xyy);
+    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
+    o[0] = w0 * (drho - C(1.5) * (a2xx + a2yy));
+    o[1] = w1 * (c13 + o13);
+    o[3] = w1 * (c13 - o13);
+    o[2] = w1 * (c24 + o24);
+    o[4] = w1 * (c24 - o24);
+    o[5] = w5 * (c57 + o57);
+    o[7] = w5 * (c57 - o57);
+    o[6] = w5 * (c68 + o68);
+    o[8] = w5 * (c68 - o68);
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+}
+
+// Moments of one node from shifted populations (eq11).
+template <typename C>
+__device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, C& rho, C& ux,
+                                           C& uy) {
+    const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const C jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    rho = rho0 + drho;
+    const C inv = C(1) / rho;
+    ux = jx * inv + C(0.5) * gx;
+    uy = jy * inv + C(0.5) * gy;
+}
+
+// ---- kernels ----------------------------------------------------------------
+
+// One fused AA step (pull-stream, moments, regularized TRT collision, G_i,
+// F_i, push-back into the same slots, half-way bounce-back) for every fluid
+// node; one thread per node.  GENERAL enables walls, masks and non-periodic
+// edges; GMODE is G_LAGGED or G_OFF.
+template <typename S, bool ODD, bool GENERAL, int GMODE>
+__global__ void __launch_bounds__(256) k_step(Args<typename Fmt<S>::C> a) {
+    using C = typename Fmt<S>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    S* __restrict__ F = static_cast<S*>(a.f);
+    const long long own = (long long)y * a.pitch + x;
+    if (GENERAL && a.mask && a.mask[own] != FLUID) return;
+    long long nb[9];
+    int kind[9];
+    links<GENERAL>(a, x, y, nb, kind);
+
+    C d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
+
+    C dpx = C(0), dpy = C(0);
+    if (GMODE == G_LAGGED) {
+        const Nbh n = neighbours(a, x, y);
+        const C* Px = a.phi_in;
+        const C* Py = a.phi_in + a.plane;
+        const C pxp = (GENERAL && n.oxp) ? C(0) : Px[(long long)y * a.pitch + n.xp];
+        const C pxm = (GENERAL && n.oxm) ? C(0) : Px[(long long)y * a.pitch + n.xm];
+        const C pyp = (GENERAL && n.oyp) ? C(0) : Py[(long long)n.yp * a.pitch + x];
+        const C pym = (GENERAL && n.oym) ? C(0) : Py[(long long)n.ym * a.pitch + x];
+        dpx = C(0.5) * (pxp - pxm);
+        dpy = C(0.5) * (pyp - pym);
+    }
+    C o[9], rho, ux, uy;
+    collide<C>(d, dpx, dpy, a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, o, rho, ux, uy);
+    if (GMODE == G_LAGGED) {
+        a.phi_out[own] = rho * ux * ux * ux;
+        a.phi_out[a.plane + own] = rho * uy * uy * uy;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        C v = o[i];
+        if (GENERAL && kind[i] == K_MOVING) v -= a.corr[i];
+        long long dst;
+        if (!ODD || kind[i] != K_STREAM)
+            dst = (long long)opp(i) * a.plane + own;
+        else
+            dst = (long long)i * a.plane + nb[i];
+        F[dst] = Fmt<S>::st(v);
+    }
+}
+
+// Outlet ghosts, after a step that produced a state of parity ODD_NEW: every
+// population that a ghost s emits into a fluid node x = s + e_i is set to the
+// post-collision f*_i of the inward neighbour z = s - (1, 0); Phi(s) := Phi(z).
+template <typename S, bool ODD_NEW>
+__global__ void k_ghosts(Args<typename Fmt<S>::C> a, const int* __restrict__ ghosts, int nghost) {
+    using C = typename Fmt<S>::C;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nghost) return;
+    S* F = static_cast<S*>(a.f);
+    const int s = ghosts[g];
+    const int sx = s % a.pitch, sy = s / a.pitch;
+    int zx = sx - 1;
+    if (zx < 0) zx += a.nx;  // validated: inside the domain (periodic) and fluid
+    long long nbs[9], nbz[9];
+    int ks[9], kz[9];
+    links<true>(a, sx, sy, nbs, ks);
+    links<true>(a, zx, sy, nbz, kz);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (ks[i] != K_STREAM || a.mask[nbs[i]] != FLUID) continue;
+        // where the step stored f*_i(z)
+        long long src;
+        if (!ODD_NEW) {  // state is even: f*_i(z) went to F[i][z + e_i] or F[ibar][z]
+            src = kz[i] == K_STREAM ? (long long)i * a.plane + nbz[i]
+                                    : (long long)opp(i) * a.plane + nbz[0];
+        } else {         // state is odd: an even step wrote f*_i(z) to F[ibar][z]
+            src = (long long)opp(i) * a.plane + nbz[0];
+        }
+        // location of f_i(x) in the new state, x = s + e_i
+        const long long x_lin = nbs[i];
+        const int xx = (int)(x_lin % a.pitch), xy = (int)(x_lin / a.pitch);
+        long long nbx[9];
+        int kx[9];
+        links<true>(a, xx, xy, nbx, kx);
+        const long long dst = ODD_NEW ? pop_loc<true>(a.plane, nbx, kx, i)
+                                      : pop_loc<false>(a.plane, nbx, kx, i);
+        F[dst] = F[src];
+    }
+    a.phi_out[s] = a.phi_out[nbz[0]];
+    a.phi_out[a.plane + s] = a.phi_out[a.plane + nbz[0]];
+}
+
+}  // namespace trt

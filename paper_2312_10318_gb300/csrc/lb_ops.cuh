@@ -1,0 +1,46 @@
+// Host-side launchers of the device kernels, one instantiation per storage
+// format (lb_ops_<fmt>.cu), so the formats compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace trt {
+
+// Threads per block of the diagnostics reduction.
+constexpr int DIAG_THREADS = 256;
+
+// Format-independent description of a lattice's device state.
+struct State {
+    void* f;              // populations, S[9][ny][pitch]
+    void* phi[2];         // Phi buffers, C[2][ny][pitch]
+    int cur;              // phi[cur] holds the previous level
+    const uint8_t* mask;  // device [ny][pitch] or nullptr
+    const int* ghosts;    // device list of outlet ghost offsets
+    int nghost;
+    int nx, ny, pitch;
+    long long plane;
+    int px, py;
+    bool general;         // walls, mask or non-periodic edges present
+    int g_mode;
+    double tau1, tau2, gx, gy, rho0;
+    double wall_ux, wall_uy, wall_rho;
+    int parity;           // parity of the current level
+};
+
+template <typename S> struct Ops {
+    // One time step (plus the outlet-ghost pass); flips parity and Phi buffers.
+    static cudaError_t step(State& s, cudaStream_t st);
+    static cudaError_t phi_static(State& s, cudaStream_t st);
+    static cudaError_t init(State& s, const double* rho, const double* ux, const double* uy,
+                            cudaStream_t st);
+    static cudaError_t moments(const State& s, double* rho, double* ux, double* uy,
+                               cudaStream_t st);
+    static cudaError_t get_f(const State& s, double* f, double* phi, cudaStream_t st);
+    static cudaError_t set_f(State& s, const double* f, const double* phi, cudaStream_t st);
+    // Deterministic FP64 diagnostics; part holds diag_blocks() * 8 doubles.
+    static cudaError_t diagnostics(const State& s, double* part, double* out, cudaStream_t st);
+};
+
+int diag_blocks(const State& s);
+
+}  // namespace trt

@@ -1,0 +1,149 @@
+// Definitions of Ops<S> (lb_ops.cuh); included once per storage format.
+#pragma once
+#include "lb_aux.cuh"
+#include "lb_ops.cuh"
+
+namespace trt {
+
+template <typename C>
+static Args<C> make_args(const State& s, bool swap_phi = false) {
+    Args<C> a;
+    a.f = s.f;
+    const int in = swap_phi ? 1 - s.cur : s.cur;
+    a.phi_in = static_cast<const C*>(s.phi[in]);
+    a.phi_out = static_cast<C*>(s.phi[1 - in]);
+    a.mask = s.mask;
+    a.nx = s.nx; a.ny = s.ny; a.pitch = s.pitch; a.plane = s.plane;
+    a.px = s.px; a.py = s.py;
+    a.k1 = (C)(1.0 - 1.0 / s.tau1);
+    a.k2 = (C)(1.0 - 1.0 / s.tau2);
+    a.kf = (C)(1.0 - 1.0 / (2.0 * s.tau1));
+    a.gx = (C)s.gx; a.gy = (C)s.gy; a.rho0 = (C)s.rho0;
+    for (int i = 0; i < 9; ++i) {
+        // 2 w_i rho_w (e_i.u_w) / c_s^2, subtracted from f*_i when e_i points
+        // into a moving wall (Ladd's correction)
+        const double eu = ex(i) * s.wall_ux + ey(i) * s.wall_uy;
+        a.corr[i] = (C)(6.0 * wgt(i) * s.wall_rho * eu);
+    }
+    return a;
+}
+
+static inline dim3 grid2d(const State& s, dim3 b) {
+    return dim3((s.nx + b.x - 1) / b.x, (s.ny + b.y - 1) / b.y);
+}
+
+template <typename S, bool ODD>
+static void launch_step(const State& s, const Args<typename Fmt<S>::C>& a, cudaStream_t st) {
+    const dim3 b(128, 2);
+    const dim3 g = grid2d(s, b);
+    if (s.general) {
+        if (s.g_mode == G_OFF) k_step<S, ODD, true, G_OFF><<<g, b, 0, st>>>(a);
+        else k_step<S, ODD, true, G_LAGGED><<<g, b, 0, st>>>(a);
+    } else {
+        if (s.g_mode == G_OFF) k_step<S, ODD, false, G_OFF><<<g, b, 0, st>>>(a);
+        else k_step<S, ODD, false, G_LAGGED><<<g, b, 0, st>>>(a);
+    }
+}
+
+template <typename S>
+cudaError_t Ops<S>::step(State& s, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    const Args<C> a = make_args<C>(s);
+    if (s.parity == 0) launch_step<S, false>(s, a, st);
+    else launch_step<S, true>(s, a, st);
+    if (s.nghost > 0) {
+        const int t = 128, g = (s.nghost + t - 1) / t;
+        if (s.parity == 0) k_ghosts<S, true><<<g, t, 0, st>>>(a, s.ghosts, s.nghost);
+        else k_ghosts<S, false><<<g, t, 0, st>>>(a, s.ghosts, s.nghost);
+    }
+    s.parity ^= 1;
+    if (s.g_mode == G_LAGGED) s.cur ^= 1;
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::phi_static(State& s, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    cudaError_t e = cudaMemsetAsync(s.phi[0], 0, sizeof(C) * 2 * s.plane, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.phi[1], 0, sizeof(C) * 2 * s.plane, st);
+    if (e != cudaSuccess) return e;
+    if (!s.mask) return cudaSuccess;
+    const dim3 b(32, 8);
+    const C inx = (C)(s.wall_rho * s.wall_ux * s.wall_ux * s.wall_ux);
+    const C iny = (C)(s.wall_rho * s.wall_uy * s.wall_uy * s.wall_uy);
+    k_phi_static<C><<<grid2d(s, b), b, 0, st>>>(s.mask, s.nx, s.ny, s.pitch, s.plane,
+                                                static_cast<C*>(s.phi[0]),
+                                                static_cast<C*>(s.phi[1]), inx, iny);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::init(State& s, const double* rho, const double* ux, const double* uy,
+                         cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    s.parity = 0;
+    s.cur = 0;
+    const Args<C> a = make_args<C>(s, /*swap_phi=*/true);  // phi_out = phi[0] (the "in" level)
+    const dim3 b(32, 8);
+    k_init<S><<<grid2d(s, b), b, 0, st>>>(a, rho, ux, uy, s.rho0, s.gx, s.gy,
+                                          static_cast<C*>(s.phi[1]));
+    if (s.nghost > 0) {
+        const int t = 128, g = (s.nghost + t - 1) / t;
+        for (int q = 0; q < 2; ++q)
+            k_ghost_phi<C><<<g, t, 0, st>>>(s.ghosts, s.nghost, s.nx, s.pitch, s.plane,
+                                            static_cast<C*>(s.phi[q]));
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::moments(const State& s, double* rho, double* ux, double* uy,
+                            cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    const Args<C> a = make_args<C>(s);
+    const dim3 b(32, 8);
+    if (s.parity) k_moments<S, true><<<grid2d(s, b), b, 0, st>>>(a, rho, ux, uy);
+    else k_moments<S, false><<<grid2d(s, b), b, 0, st>>>(a, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::get_f(const State& s, double* f, double* phi, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    const Args<C> a = make_args<C>(s);
+    const dim3 b(32, 8);
+    if (s.parity) k_get_f<S, true><<<grid2d(s, b), b, 0, st>>>(a, f, phi);
+    else k_get_f<S, false><<<grid2d(s, b), b, 0, st>>>(a, f, phi);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::set_f(State& s, const double* f, const double* phi, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    s.parity = 0;
+    const Args<C> a = make_args<C>(s);
+    const dim3 b(32, 8);
+    k_set_f<S><<<grid2d(s, b), b, 0, st>>>(a, f, phi);
+    if (!phi) {
+        k_phi_of_state<S><<<grid2d(s, b), b, 0, st>>>(a);
+        if (s.nghost > 0) {
+            const int t = 128, g = (s.nghost + t - 1) / t;
+            k_ghost_phi<C><<<g, t, 0, st>>>(s.ghosts, s.nghost, s.nx, s.pitch, s.plane,
+                                            static_cast<C*>(s.phi[s.cur]));
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::diagnostics(const State& s, double* part, double* out, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    const Args<C> a = make_args<C>(s);
+    const int nb = diag_blocks(s);
+    if (s.parity) k_diag_partial<S, true><<<nb, DIAG_THREADS, 0, st>>>(a, part);
+    else k_diag_partial<S, false><<<nb, DIAG_THREADS, 0, st>>>(a, part);
+    k_diag_final<<<1, DIAG_THREADS, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace trt

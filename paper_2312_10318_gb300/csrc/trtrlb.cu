@@ -1,0 +1,401 @@
+// C ABI of the D2Q9 TRT-RLB library (declared in include/trtrlb.h).
+// Owns the device memory of each lattice, validates the problem statement and
+// dispatches to the per-format launchers (lb_ops.cuh).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lb_ops.cuh"
+#include "trtrlb.h"
+
+struct trtrlb_lattice {
+    trtrlb_params p;
+    trt::State s;
+    cudaStream_t stream;
+    int64_t t;           // steps since init / set_f
+    void* f;             // device allocations owned by the handle
+    void* phi;           // both Phi buffers in one allocation
+    uint8_t* mask;
+    int* ghosts;
+    double* stage;       // FP64 staging for host transfers, 11 * n
+    double* part;        // diagnostics partials (scratch)
+    double* dout;        // diagnostics result, 8 doubles
+    int64_t bytes;
+    char err[256];
+};
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+size_t elem_size(int storage) {
+    switch (storage) {
+        case TRTRLB_F64: return sizeof(double);
+        case TRTRLB_F32: return sizeof(float);
+        case TRTRLB_F16_SHIFTED: return sizeof(__half);
+        case TRTRLB_BF16_SHIFTED: return sizeof(__nv_bfloat16);
+        default: return 0;
+    }
+}
+size_t phi_size(int storage) { return storage == TRTRLB_F64 ? sizeof(double) : sizeof(float); }
+
+int fail(char* buf, int code, const char* fmt, const char* detail = nullptr) {
+    if (detail) std::snprintf(buf, 256, fmt, detail);
+    else std::snprintf(buf, 256, "%s", fmt);
+    return code;
+}
+
+int cuda_fail(char* buf, cudaError_t e, const char* where) {
+    std::snprintf(buf, 256, "%s: %s", where, cudaGetErrorString(e));
+    return TRTRLB_ECUDA;
+}
+
+bool on_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Dispatch of Ops<S> on the storage format.
+#define TRT_DISPATCH(storage, CALL)                                              \
+    [&]() -> cudaError_t {                                                       \
+        switch (storage) {                                                       \
+            case TRTRLB_F64: { using S = double; return trt::Ops<S>::CALL; }     \
+            case TRTRLB_F32: { using S = float; return trt::Ops<S>::CALL; }      \
+            case TRTRLB_F16_SHIFTED: { using S = __half; return trt::Ops<S>::CALL; } \
+            default: { using S = __nv_bfloat16; return trt::Ops<S>::CALL; }      \
+        }                                                                        \
+    }()
+
+void release(trtrlb_lattice* h) {
+    if (!h) return;
+    if (h->f) cudaFree(h->f);
+    if (h->phi) cudaFree(h->phi);
+    if (h->mask) cudaFree(h->mask);
+    if (h->ghosts) cudaFree(h->ghosts);
+    if (h->stage) cudaFree(h->stage);
+    if (h->part) cudaFree(h->part);
+    if (h->dout) cudaFree(h->dout);
+    delete h;
+}
+
+// Resolves tau_s2 from tau_s2 / magic (eq_a29).  Returns 0 or an error code.
+int resolve_tau2(const trtrlb_params& p, double* tau2, char* err) {
+    const bool has_t2 = !std::isnan(p.tau_s2), has_m = !std::isnan(p.magic);
+    if (!has_t2 && !has_m) return fail(err, TRTRLB_EINVAL, "one of tau_s2 / magic must be given");
+    double t2 = has_t2 ? p.tau_s2 : 0.5 + p.magic / (p.tau_s - 0.5);
+    if (has_t2 && has_m) {
+        const double from_m = 0.5 + p.magic / (p.tau_s - 0.5);
+        if (std::fabs(from_m - t2) > 1e-12 * std::fabs(t2))
+            return fail(err, TRTRLB_EINVAL, "tau_s2 and magic disagree");
+    }
+    if (!(t2 > 0.5) || !std::isfinite(t2))
+        return fail(err, TRTRLB_EINVAL, "tau_s2 must be finite and > 1/2 (magic > 0)");
+    *tau2 = t2;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void trtrlb_default_params(trtrlb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->nx = p->ny = 64;
+    p->periodic_x = p->periodic_y = 1;
+    p->tau_s = 0.8;
+    p->tau_s2 = NAN;
+    p->magic = 0.25;
+    p->rho0 = 1.0;
+    p->wall_rho = 1.0;
+    p->storage = TRTRLB_F32;
+    p->g_mode = TRTRLB_G_LAGGED;
+}
+
+int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, trtrlb_t* out) {
+    char* err = g_create_err;
+    err[0] = 0;
+    if (!pp || !out) return fail(err, TRTRLB_EINVAL, "null params or output handle");
+    const trtrlb_params p = *pp;
+    // grid rows are launched as gridDim.y = ceil(ny / 8) <= 65535; node offsets
+    // (including padding) fit in 32-bit integers
+    if (p.nx < 1 || p.ny < 1 || p.ny > 131070 || p.nx > (1 << 24) ||
+        ((int64_t)p.nx + 63) * p.ny > (int64_t)1 << 30)
+        return fail(err, TRTRLB_EINVAL, "lattice size out of range");
+    if (!(p.tau_s > 0.5) || !std::isfinite(p.tau_s))
+        return fail(err, TRTRLB_EINVAL, "tau_s must be finite and > 1/2");
+    double tau2 = 0;
+    if (int rc = resolve_tau2(p, &tau2, err)) return rc;
+    if (elem_size(p.storage) == 0) return fail(err, TRTRLB_EINVAL, "unknown storage format");
+    if (p.g_mode == TRTRLB_G_CURRENT)
+        return fail(err, TRTRLB_ENOTSUP, "G_CURRENT is not built into the in-place AA kernel");
+    if (p.g_mode != TRTRLB_G_LAGGED && p.g_mode != TRTRLB_G_OFF)
+        return fail(err, TRTRLB_EINVAL, "unknown g_mode");
+    if (!(p.rho0 > 0) || !std::isfinite(p.gx) || !std::isfinite(p.gy) ||
+        !std::isfinite(p.wall_ux) || !std::isfinite(p.wall_uy) || !std::isfinite(p.wall_rho))
+        return fail(err, TRTRLB_EINVAL, "rho0 must be > 0 and forces / wall state finite");
+
+    const int pitch = (p.nx + 63) / 64 * 64;
+    const long long plane = (long long)pitch * p.ny;
+    const long long n = (long long)p.nx * p.ny;
+    std::vector<int> ghosts;
+    if (mask) {
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                const uint8_t c = mask[(long long)y * p.nx + x];
+                if (c > TRTRLB_OUTLET) return fail(err, TRTRLB_EINVAL, "mask class out of range");
+                if (c != TRTRLB_OUTLET) continue;
+                int zx = x - 1;
+                if (zx < 0) {
+                    if (!p.periodic_x) return fail(err, TRTRLB_EINVAL, "outlet ghost without inward neighbour");
+                    zx += p.nx;
+                }
+                if (mask[(long long)y * p.nx + zx] != TRTRLB_FLUID)
+                    return fail(err, TRTRLB_EINVAL, "outlet ghost's inward neighbour (x-1,y) must be fluid");
+                // the inward neighbour's links toward -x must not end at a moving wall
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int qx = zx - 1, qy = y + dy;
+                    if (qx < 0) { if (!p.periodic_x) continue; qx += p.nx; }
+                    if (qy < 0 || qy >= p.ny) { if (!p.periodic_y) continue; qy = (qy + p.ny) % p.ny; }
+                    if (mask[(long long)qy * p.nx + qx] == TRTRLB_INLET)
+                        return fail(err, TRTRLB_EINVAL, "outlet ghost too close to an inlet");
+                }
+                ghosts.push_back((int)((long long)y * pitch + x));
+            }
+    }
+
+    trtrlb_lattice* h = new (std::nothrow) trtrlb_lattice();
+    if (!h) return fail(err, TRTRLB_ENOMEM, "host allocation failed");
+    h->p = p;
+    h->p.tau_s2 = tau2;
+    h->p.magic = (p.tau_s - 0.5) * (tau2 - 0.5);
+    h->stream = static_cast<cudaStream_t>(stream);
+    const size_t es = elem_size(p.storage), ps = phi_size(p.storage);
+    cudaError_t e;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        e = cudaMalloc(ptr, bytes);
+        if (e == cudaSuccess) h->bytes += (int64_t)bytes;
+        return e == cudaSuccess;
+    };
+    bool ok = alloc(&h->f, es * 9 * plane) && alloc(&h->phi, ps * 4 * plane) &&
+              alloc((void**)&h->stage, sizeof(double) * 11 * n) &&
+              alloc((void**)&h->dout, sizeof(double) * 8);
+    if (ok && mask) ok = alloc((void**)&h->mask, (size_t)plane);
+    if (ok && !ghosts.empty()) ok = alloc((void**)&h->ghosts, sizeof(int) * ghosts.size());
+    trt::State& s = h->s;
+    s.f = h->f;
+    s.phi[0] = h->phi;
+    s.phi[1] = static_cast<char*>(h->phi) + ps * 2 * plane;
+    s.cur = 0;
+    s.mask = h->mask;
+    s.ghosts = h->ghosts;
+    s.nghost = (int)ghosts.size();
+    s.nx = p.nx; s.ny = p.ny; s.pitch = pitch; s.plane = plane;
+    s.px = p.periodic_x ? 1 : 0; s.py = p.periodic_y ? 1 : 0;
+    s.general = mask != nullptr || !p.periodic_x || !p.periodic_y;
+    s.g_mode = p.g_mode;
+    s.tau1 = p.tau_s; s.tau2 = tau2;
+    s.gx = p.gx; s.gy = p.gy; s.rho0 = p.rho0;
+    s.wall_ux = p.wall_ux; s.wall_uy = p.wall_uy; s.wall_rho = p.wall_rho;
+    s.parity = 0;
+    if (ok) ok = alloc((void**)&h->part, sizeof(double) * 8 * trt::diag_blocks(s));
+    if (!ok) {
+        const int rc = e == cudaErrorMemoryAllocation ? TRTRLB_ENOMEM : TRTRLB_ECUDA;
+        std::snprintf(err, 256, "cudaMalloc: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        release(h);
+        return rc;
+    }
+    if (mask) {
+        // pitched copy of the mask; padding columns are marked solid
+        std::vector<uint8_t> m((size_t)plane, TRTRLB_SOLID);
+        for (int y = 0; y < p.ny; ++y)
+            std::memcpy(&m[(size_t)y * pitch], mask + (size_t)y * p.nx, p.nx);
+        e = cudaMemcpy(h->mask, m.data(), (size_t)plane, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !ghosts.empty())
+            e = cudaMemcpy(h->ghosts, ghosts.data(), sizeof(int) * ghosts.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            const int rc = cuda_fail(err, e, "mask upload");
+            release(h);
+            return rc;
+        }
+    }
+    e = cudaMemsetAsync(h->f, 0, es * 9 * plane, h->stream);
+    if (e == cudaSuccess) e = TRT_DISPATCH(p.storage, phi_static(h->s, h->stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(err, e, "create");
+        release(h);
+        return rc;
+    }
+    h->t = 0;
+    *out = h;
+    return TRTRLB_OK;
+}
+
+int trtrlb_destroy(trtrlb_t h) {
+    if (!h) return TRTRLB_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    return TRTRLB_OK;
+}
+
+int trtrlb_set_stream(trtrlb_t h, void* stream) {
+    if (!h) return TRTRLB_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return TRTRLB_OK;
+}
+
+int trtrlb_init(trtrlb_t h, const double* rho, const double* ux, const double* uy) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (!ux || !uy) return fail(h->err, TRTRLB_EINVAL, "ux and uy are required");
+    const size_t n = (size_t)h->p.nx * h->p.ny, nb = n * sizeof(double);
+    const double* src[3] = {rho, ux, uy};
+    const double* dev[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+        if (!src[q]) continue;
+        if (on_device(src[q])) {
+            dev[q] = src[q];
+        } else {
+            e = cudaMemcpyAsync(h->stage + q * n, src[q], nb, cudaMemcpyHostToDevice, h->stream);
+            dev[q] = h->stage + q * n;
+        }
+    }
+    if (e == cudaSuccess) e = TRT_DISPATCH(h->p.storage, init(h->s, dev[0], dev[1], dev[2], h->stream));
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "init");
+    h->t = 0;
+    return TRTRLB_OK;
+}
+
+int trtrlb_step(trtrlb_t h, int64_t nsteps) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (nsteps < 0) return fail(h->err, TRTRLB_EINVAL, "nsteps must be >= 0");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const cudaError_t e = TRT_DISPATCH(h->p.storage, step(h->s, h->stream));
+        if (e != cudaSuccess) return cuda_fail(h->err, e, "step");
+        ++h->t;
+    }
+    return TRTRLB_OK;
+}
+
+int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    const size_t n = (size_t)h->p.nx * h->p.ny, nb = n * sizeof(double);
+    double* dst[3] = {rho, ux, uy};
+    double* dev[3] = {nullptr, nullptr, nullptr};
+    bool host = false;
+    for (int q = 0; q < 3; ++q) {
+        if (!dst[q]) continue;
+        if (on_device(dst[q])) dev[q] = dst[q];
+        else { dev[q] = h->stage + q * n; host = true; }
+    }
+    cudaError_t e = TRT_DISPATCH(h->p.storage, moments(h->s, dev[0], dev[1], dev[2], h->stream));
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        if (dst[q] && dev[q] != dst[q])
+            e = cudaMemcpyAsync(dst[q], dev[q], nb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && host) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "moments");
+    return TRTRLB_OK;
+}
+
+int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    double* df = f && !on_device(f) ? h->stage : f;
+    double* dp = phi && !on_device(phi) ? h->stage + 9 * n : phi;
+    cudaError_t e = TRT_DISPATCH(h->p.storage, get_f(h->s, df, dp, h->stream));
+    bool host = false;
+    if (e == cudaSuccess && f && df != f) {
+        e = cudaMemcpyAsync(f, df, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        host = true;
+    }
+    if (e == cudaSuccess && phi && dp != phi) {
+        e = cudaMemcpyAsync(phi, dp, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        host = true;
+    }
+    if (e == cudaSuccess && host) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "get_f");
+    return TRTRLB_OK;
+}
+
+int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (!f) return fail(h->err, TRTRLB_EINVAL, "f is required");
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    const double* df = f;
+    const double* dp = phi;
+    cudaError_t e = cudaSuccess;
+    if (!on_device(f)) {
+        e = cudaMemcpyAsync(h->stage, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        df = h->stage;
+    }
+    if (e == cudaSuccess && phi && !on_device(phi)) {
+        e = cudaMemcpyAsync(h->stage + 9 * n, phi, 2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream);
+        dp = h->stage + 9 * n;
+    }
+    if (e == cudaSuccess) e = TRT_DISPATCH(h->p.storage, set_f(h->s, df, dp, h->stream));
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "set_f");
+    h->t = 0;
+    return TRTRLB_OK;
+}
+
+int64_t trtrlb_time(trtrlb_t h) { return h ? h->t : -1; }
+
+int trtrlb_diagnostics(trtrlb_t h, double* out) {
+    if (!h || !out) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    const bool dev = on_device(out);
+    cudaError_t e = TRT_DISPATCH(h->p.storage, diagnostics(h->s, h->part, dev ? out : h->dout, h->stream));
+    if (e == cudaSuccess && !dev) {
+        e = cudaMemcpyAsync(out, h->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "diagnostics");
+    return TRTRLB_OK;
+}
+
+int64_t trtrlb_device_bytes(trtrlb_t h) { return h ? h->bytes : -1; }
+
+const char* trtrlb_strerror(int code) {
+    switch (code) {
+        case TRTRLB_OK: return "ok";
+        case TRTRLB_EINVAL: return "invalid argument";
+        case TRTRLB_ENOMEM: return "out of memory";
+        case TRTRLB_ECUDA: return "CUDA error";
+        case TRTRLB_EUNSTABLE: return "unstable state (NaN/Inf or velocity bound exceeded)";
+        case TRTRLB_ETIMEOUT: return "bounded wait timed out";
+        case TRTRLB_ENOTSUP: return "not supported by this build";
+        default: return "unknown error";
+    }
+}
+
+const char* trtrlb_last_error(trtrlb_t h) { return h ? h->err : g_create_err; }
+
+}  // extern "C"
+
+namespace trt {
+int diag_blocks(const State& s) {
+    const long long n = (long long)s.nx * s.ny;
+    long long b = (n + DIAG_THREADS - 1) / DIAG_THREADS;
+    return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+}
+}  // namespace trt

@@ -1,0 +1,176 @@
+"""Python binding of one D2Q9 TRT-RLB lattice (argument marshalling only).
+
+Every step of the method runs in ``libtrtrlb.so``; this module converts
+arguments, owns the handle and raises on error codes.  Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA), float64 and C-contiguous, with
+the layouts of ``include/trtrlb.h``: fields ``[ny, nx]``, populations
+``[9, ny, nx]``, Phi ``[2, ny, nx]``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import _lib
+
+STORAGE = {"f64": _lib.F64, "f32": _lib.F32, "f16": _lib.F16_SHIFTED, "bf16": _lib.BF16_SHIFTED}
+G_MODE = {"lagged": _lib.G_LAGGED, "current": _lib.G_CURRENT, "off": _lib.G_OFF}
+
+
+def _ptr(a, shape=None):
+    """Raw pointer of a float64 contiguous numpy array / torch tensor (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy arrays must be float64 and C-contiguous")
+        if shape is not None and a.shape != shape:
+            raise ValueError(f"expected shape {shape}, got {a.shape}")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch tensors must be float64 and contiguous")
+        if shape is not None and tuple(a.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as_f64(a, shape):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+    return a
+
+
+class Lattice:
+    """One lattice on the current CUDA device.
+
+    tau_s is tau_{s,1}; give tau_s2 (tau_{s,2}) or magic (Lambda_s, eq_a29).
+    periodic: (x, y); a non-periodic direction has stationary half-way
+    bounce-back walls just outside the domain.  g: body acceleration (F = rho
+    g).  mask: [ny, nx] uint8 of node classes (0 fluid, 1 solid, 2 inlet, 3
+    outlet ghost) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16'.
+    g_mode: 'lagged' | 'off'.  stream: a torch.cuda.Stream or raw handle
+    (default: the current torch stream).
+    """
+
+    def __init__(self, nx, ny, tau_s, *, tau_s2=None, magic=None, periodic=(True, True),
+                 g=(0.0, 0.0), rho0=1.0, wall_u=(0.0, 0.0), wall_rho=1.0, storage="f32",
+                 g_mode="lagged", mask=None, stream=None):
+        lib = _lib.load()
+        p = _lib.Params()
+        lib.trtrlb_default_params(C.byref(p))
+        p.nx, p.ny = int(nx), int(ny)
+        p.periodic_x, p.periodic_y = int(bool(periodic[0])), int(bool(periodic[1]))
+        p.tau_s = float(tau_s)
+        p.tau_s2 = math.nan if tau_s2 is None else float(tau_s2)
+        p.magic = math.nan if magic is None else float(magic)
+        p.gx, p.gy = float(g[0]), float(g[1])
+        p.rho0 = float(rho0)
+        p.wall_ux, p.wall_uy = float(wall_u[0]), float(wall_u[1])
+        p.wall_rho = float(wall_rho)
+        p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        p.g_mode = G_MODE[g_mode] if isinstance(g_mode, str) else int(g_mode)
+        self.nx, self.ny, self.storage = p.nx, p.ny, storage
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            if m.shape != (self.ny, self.nx):
+                raise ValueError("mask must be [ny, nx]")
+        self._mask = m
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        _lib.check(lib.trtrlb_create(C.byref(p), None if m is None else m.ctypes.data,
+                                     C.c_void_p(stream), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.params = p
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.trtrlb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, rc):
+        return _lib.check(rc, self._h)
+
+    # -- state ----------------------------------------------------------------
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    @property
+    def t(self) -> int:
+        return int(self._lib.trtrlb_time(self._h))
+
+    @property
+    def tau_s2(self) -> float:
+        return self.params.tau_s2
+
+    def device_bytes(self) -> int:
+        return int(self._lib.trtrlb_device_bytes(self._h))
+
+    def set_stream(self, stream):
+        s = stream if isinstance(stream, int) else stream.cuda_stream
+        self._chk(self._lib.trtrlb_set_stream(self._h, C.c_void_p(s)))
+
+    def init(self, ux, uy, rho=None):
+        """Initial state from (rho, u) (rho None: rho0)."""
+        sh = self.shape
+        ux, uy, rho = _as_f64(ux, sh), _as_f64(uy, sh), _as_f64(rho, sh)
+        self._chk(self._lib.trtrlb_init(self._h, _ptr(rho, sh), _ptr(ux, sh), _ptr(uy, sh)))
+        return self
+
+    def step(self, n: int = 1):
+        self._chk(self._lib.trtrlb_step(self._h, int(n)))
+        return self
+
+    def moments(self, rho=None, ux=None, uy=None):
+        """(rho, ux, uy) of the current state.  Without outputs: new host arrays."""
+        sh = self.shape
+        if rho is None and ux is None and uy is None:
+            rho, ux, uy = (np.empty(sh) for _ in range(3))
+        self._chk(self._lib.trtrlb_moments(self._h, _ptr(rho, sh), _ptr(ux, sh), _ptr(uy, sh)))
+        return rho, ux, uy
+
+    def get_f(self, with_phi=False):
+        f = np.empty((9, self.ny, self.nx))
+        phi = np.empty((2, self.ny, self.nx)) if with_phi else None
+        self._chk(self._lib.trtrlb_get_f(self._h, _ptr(f), _ptr(phi)))
+        return (f, phi) if with_phi else f
+
+    def set_f(self, f, phi=None):
+        f = _as_f64(f, (9, self.ny, self.nx))
+        phi = _as_f64(phi, (2, self.ny, self.nx))
+        self._chk(self._lib.trtrlb_set_f(self._h, _ptr(f, (9, self.ny, self.nx)),
+                                         _ptr(phi, (2, self.ny, self.nx))))
+        return self
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(8)
+        self._chk(self._lib.trtrlb_diagnostics(self._h, _ptr(out)))
+        keys = ("mass", "momentum_x", "momentum_y", "kinetic_energy", "max_u", "nonfinite",
+                "wall_force_x", "wall_force_y")
+        return dict(zip(keys, out.tolist()))

@@ -1,0 +1,68 @@
+"""Reduced-precision storage (FP32, shifted FP16 / BF16; FP32 arithmetic) against
+the FP64 oracle: the error each mode reaches on the paper's problems, with the
+bound each mode states."""
+import numpy as np
+import pytest
+
+from helpers import field_errors, gpu_lattice, oracle_lattice, rel
+from paper_2312_10318_gb300 import params as P
+from paper_2312_10318_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# stated velocity bounds (||u - u_oracle||_inf / ||u_oracle||_inf) for 1000
+# Taylor-Green steps on 64^2 (u0 = 0.04, Re = 100)
+TG_BOUND = {"f64": 1e-10, "f32": 3e-5, "f16": 1.5e-2, "bf16": 2e-1}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_taylor_green_reduced_precision(gpu_lib, storage):
+    pr = W.taylor_green(64, 0.04, 100.0, magic=0.25)
+    G = gpu_lattice(pr, storage).init(pr.ux, pr.uy, pr.rho)
+    R = oracle_lattice(pr).init(pr.ux, pr.uy, pr.rho)
+    G.step(1000)
+    R.step(1000)
+    e = field_errors(G, R)
+    print(f"TG64 {storage}: ux {e['ux']:.3e} uy {e['uy']:.3e} rho {e['rho']:.3e}")
+    assert max(e["ux"], e["uy"]) < TG_BOUND[storage], e
+
+
+def test_double_shear_layer_fp32_prefix(gpu_lib):
+    """Double shear layer 256^2 at Re = 1e5 (tau1 near 1/2): a 200-step prefix in FP32
+    against the FP64 oracle."""
+    pr = W.double_shear_layer(256, re=1e5)
+    G = gpu_lattice(pr, "f32").init(pr.ux, pr.uy)
+    R = oracle_lattice(pr).init(pr.ux, pr.uy)
+    G.step(200)
+    R.step(200)
+    e = field_errors(G, R)
+    print(f"DSL256 f32 200 steps: ux {e['ux']:.3e} uy {e['uy']:.3e} rho {e['rho']:.3e}")
+    assert max(e["ux"], e["uy"]) < 1e-4, e
+
+
+def test_full_size_double_shear_layer_fp32(gpu_lib):
+    """The benchmark lattice (1024^2, FP32 storage) against the oracle for 3 steps,
+    element by element."""
+    pr = W.double_shear_layer(1024, re=1e4)
+    G = gpu_lattice(pr, "f32").init(pr.ux, pr.uy)
+    R = oracle_lattice(pr).init(pr.ux, pr.uy)
+    G.step(3)
+    R.step(3)
+    e = field_errors(G, R)
+    print(f"DSL1024 f32 3 steps: {max(e.values()):.3e}")
+    assert max(e["ux"], e["uy"]) < 1e-5, e
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_poiseuille_reduced_precision(gpu_lib, storage):
+    ny, u_c, tau1, magic = 32, 0.01, 1.0, 3 / 16
+    nu = P.nu_from_tau(tau1)
+    y = np.arange(1, ny + 1) - 0.5
+    exact = 4 * u_c / ny ** 2 * y * (ny - y)
+    pr = W.poiseuille(ny, tau1, magic, nx=8, u_c=u_c, profile=exact)
+    G = gpu_lattice(pr, storage).init(pr.ux, pr.uy)
+    G.step(60000)
+    _, ux, _ = G.moments()
+    err = np.abs(ux - exact[:, None]).max() / u_c
+    print(f"Poiseuille {storage}: {err:.3e}")
+    assert err < {"f32": 1e-4, "f16": 5e-2}[storage]
