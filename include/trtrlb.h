@@ -150,6 +150,32 @@ int64_t trtrlb_time(trtrlb_t h);
  * out may be host or device memory. */
 int trtrlb_diagnostics(trtrlb_t h, double* out);
 
+/* The same eight diagnostics as trtrlb_diagnostics, for a state given in the
+ * canonical layout, computed without allocating any memory.  The paper has no
+ * counterpart; this is for callers that cannot call cudaMalloc when they need
+ * the numbers: code running while a stream is captured into a CUDA graph, code
+ * bound to a fixed device budget or memory pool it manages itself, and
+ * latency-critical loops that must not take an allocation's implicit sync.
+ *   f      : device, 9*nx*ny FP64 populations (layout above; e.g. what
+ *            trtrlb_get_f writes), read only;
+ *   mask   : device, nx*ny bytes of TRTRLB_* classes, or NULL (all fluid);
+ *   periodic_x/y, gx, gy : as in trtrlb_params (u includes the g/2 shift);
+ *   out    : device, 8 doubles, same meaning as in trtrlb_diagnostics;
+ *   stream : cudaStream_t the two kernels run on (asynchronous).
+ * The reduction's partial sums live in one static device array of 512 KiB
+ * (8 doubles for each of at most 8192 blocks of 2048 nodes) that every GPU
+ * loading the library holds until the process exits.  Lattices of more than
+ * 16,777,216 nodes (4096^2) are rejected with TRTRLB_EINVAL, as are null or
+ * host pointers.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and caches it: make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams, or on several host threads) race and corrupt each
+ * other's results; serialise them.  Nothing needs clearing between calls:
+ * every call overwrites the partial sums it reads. */
+int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx, int32_t ny,
+                               int32_t periodic_x, int32_t periodic_y, double gx, double gy,
+                               double* out, void* stream);
+
 /* Device bytes held by the handle. */
 int64_t trtrlb_device_bytes(trtrlb_t h);
 

@@ -45,6 +45,8 @@ SIGNATURES = {
     "trtrlb_set_f": (C.c_int, [_vp, _dp, _dp]),
     "trtrlb_time": (C.c_int64, [_vp]),
     "trtrlb_diagnostics": (C.c_int, [_vp, _dp]),
+    "trtrlb_diagnostics_noalloc": (C.c_int, [_dp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_double, C.c_double, _dp, _vp]),
     "trtrlb_device_bytes": (C.c_int64, [_vp]),
     "trtrlb_strerror": (C.c_char_p, [C.c_int]),
     "trtrlb_last_error": (C.c_char_p, [_vp]),
