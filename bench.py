@@ -4,8 +4,9 @@
 Default workload: the double shear layer (Sec. III A) on three 1024 x 1024
 periodic lattices, Re = 1e4, 1e5, 1e7 (kappa = 80, delta = 0.05, u_c = 0.04,
 tau_{s,2} = 0.625), FP32 storage, lagged G.  One benchmark step is one time
-step of all three lattices.  The L2 cache is flushed (512 MiB memset) before
-every timed step; each step is timed with CUDA events on the launching stream.
+step of all three lattices.  The L2 cache is flushed before every timed step
+(a 512 MiB buffer written, then read so no dirty flush lines remain); each step
+is timed with CUDA events on the launching stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -239,6 +240,8 @@ def main():
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--e2e-steps", type=int, default=100, help="time steps per end-to-end solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="batch", choices=["batch", "single"],
+                    help="batch: one launch per time step for all lattices; single: one per lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -249,6 +252,7 @@ def main():
     import numpy as np
     import torch
     from paper_2312_10318_gb300 import Lattice
+    from paper_2312_10318_gb300.lattice import Batch
 
     world, rank, local = dist_setup()
     if args.gpus != world:
@@ -264,7 +268,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     lats = []
     for pr in problems:
         lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode="lagged", stream=stream,
@@ -274,11 +279,26 @@ def main():
         lats.append(lat)
     nodes = sum(p.nodes for p in problems)
     flush = torch.empty(args.flush_mib << 20, dtype=torch.uint8, device="cuda")
+    # all lattices of the workload advance in one launch per time step
+    batch = Batch(stream).set(lats)
 
-    for _ in range(args.warmup):
+    def advance(n):
+        if args.mode == "batch":
+            batch.step(n)
+        else:
+            for lat in lats:
+                lat.step(n)
+
+    def flush_l2():
+        # write a buffer 4x the L2, then read it back, so L2 holds only clean
+        # lines of the flush buffer (no dirty write-backs charged to the step)
         flush.zero_()
-        for lat in lats:
-            lat.step(1)
+        flush_sink.copy_(flush.view(torch.int64).sum())
+
+    flush_sink = torch.empty((), dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup):
+        flush_l2()
+        advance(1)
     barrier()
 
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -288,12 +308,11 @@ def main():
     events = []
     barrier()
     for _ in range(args.steps):
-        flush.zero_()
+        flush_l2()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for lat in lats:
-            lat.step(1)
+        advance(1)
         e1.record(stream)
         events.append((e0, e1))
     barrier()
@@ -308,9 +327,10 @@ def main():
     value = nodes * args.steps * world / (total_ms / 1e3) / 1e6
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
-    launches = args.steps * len(lats)
+    per_step_launches = 1 if args.mode == "batch" else len(lats)
+    launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
-    per_launch_bytes = bytes_per_node(storage) * nodes / len(lats)
+    per_launch_bytes = bytes_per_node(storage) * nodes / per_step_launches
     achieved = per_launch_bytes / launch_s / 1e9
     peak, peak_kind = hbm_peak()
     traffic = recorded_traffic(args.workload)
@@ -326,8 +346,7 @@ def main():
         t0 = time.perf_counter()
         for lat, (ux, uy, rho) in zip(lats, host_in):
             lat.init(ux, uy, rho)
-        for lat in lats:
-            lat.step(args.e2e_steps)
+        advance(args.e2e_steps)
         for lat, out in zip(lats, host_out):
             lat.moments(*out)
         torch.cuda.synchronize()
@@ -348,11 +367,15 @@ def main():
             "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
                        "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
                        "g_mode": "lagged", "parallelism": f"replicas x{world}",
-                       "l2": f"{args.flush_mib} MiB memset before every timed step (outside the events)"},
+                       "launch": "one batched kernel per time step" if args.mode == "batch"
+                                 else "one kernel per lattice and time step",
+                       "l2": f"{args.flush_mib} MiB written then read before every timed step "
+                             "(outside the events)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic is None else traffic,
-                         "kernel": "trt::k_step (fused AA stream-collide)",
+                         "kernel": "trt::k_step_batch (fused AA stream-collide, all lattices)"
+                                   if args.mode == "batch" else "trt::k_step (fused AA stream-collide)",
                          "algorithmic_bytes_per_node": bytes_per_node(storage),
                          "launch_ms": launch_s * 1e3},
             "e2e": {"value": e2e_value, "unit": UNIT,
@@ -365,6 +388,7 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(problems)
         print(json.dumps(line), flush=True)
+    batch.close()
     for lat in lats:
         lat.close()
     if dist is not None:

@@ -176,6 +176,34 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
                                int32_t periodic_x, int32_t periodic_y, double gx, double gy,
                                double* out, void* stream);
 
+/* ---- batches ---------------------------------------------------------------
+ * A batch advances several lattices together: per time step one kernel launch
+ * per storage format covers every tile of every lattice in the batch (the
+ * same per-node update as trtrlb_step, so results are those of stepping each
+ * lattice alone).  Runs of 32 or more steps replay a captured CUDA graph when
+ * the batch's stream is not the legacy default stream.  Lattices keep their
+ * own parity and step count; all of them must live on the batch's device and
+ * their other work must be ordered with the batch's stream by the caller
+ * (simplest: create them on the same stream).  A lattice must stay alive while
+ * it is a member; call trtrlb_batch_set again before destroying it. */
+typedef struct trtrlb_batch* trtrlb_batch_t;
+
+/* Creates an empty batch ordered on `stream` (cudaStream_t; NULL = legacy). */
+int trtrlb_batch_create(void* stream, trtrlb_batch_t* out);
+
+/* Replaces the members (count >= 0 distinct handles).  EINVAL on a null or
+ * repeated handle.  Invalidates the captured graph. */
+int trtrlb_batch_set(trtrlb_batch_t b, const trtrlb_t* lattices, int count);
+
+/* Advances every member by nsteps >= 0 steps (asynchronous). */
+int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps);
+
+/* Frees the batch (not its lattices); synchronises its stream. */
+int trtrlb_batch_destroy(trtrlb_batch_t b);
+
+/* Message of the batch's last error ("" if none). */
+const char* trtrlb_batch_last_error(trtrlb_batch_t b);
+
 /* Device bytes held by the handle. */
 int64_t trtrlb_device_bytes(trtrlb_t h);
 

@@ -48,6 +48,11 @@ SIGNATURES = {
     "trtrlb_diagnostics_noalloc": (C.c_int, [_dp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_double, C.c_double, _dp, _vp]),
     "trtrlb_device_bytes": (C.c_int64, [_vp]),
+    "trtrlb_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
+    "trtrlb_batch_set": (C.c_int, [_vp, C.POINTER(_vp), C.c_int]),
+    "trtrlb_batch_step": (C.c_int, [_vp, _i64]),
+    "trtrlb_batch_destroy": (C.c_int, [_vp]),
+    "trtrlb_batch_last_error": (C.c_char_p, [_vp]),
     "trtrlb_strerror": (C.c_char_p, [C.c_int]),
     "trtrlb_last_error": (C.c_char_p, [_vp]),
 }

@@ -1,0 +1,40 @@
+// Batched step: one launch advances a group of lattices that share storage
+// format, boundary flavour, G mode and the parity of their current level.  The
+// lattices' arguments travel in the kernel's parameter space (constant bank),
+// so a CTA finds its lattice and reads its coefficients with uniform constant
+// loads; the per-node body is the fully specialised node_step.
+#pragma once
+#include "lb_device.cuh"
+
+namespace trt {
+
+constexpr int BATCH_THREADS = 256;
+
+template <typename C, int MAXL> struct GroupParams {
+    int n;                       // lattices in this launch
+    int tile_begin[MAXL + 1];    // prefix sums of tiles; tile_begin[n] = total
+    int tiles_x[MAXL];           // tiles per tile row
+    int log2_tw[MAXL];           // tile width 2^log2_tw nodes, height 256 / width
+    Args<C> a[MAXL];
+};
+
+template <typename S, bool ODD, bool GENERAL, int GMODE, int MAXL>
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_step_group(const __grid_constant__ GroupParams<typename Fmt<S>::C, MAXL> p) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = p.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tile_begin[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int lt = p.log2_tw[lo];
+    const int t = b - p.tile_begin[lo];
+    const int tx = t % p.tiles_x[lo], ty = t / p.tiles_x[lo];
+    const int x = (tx << lt) + ((int)threadIdx.x & ((1 << lt) - 1));
+    const int y = (ty << (8 - lt)) + ((int)threadIdx.x >> lt);
+    if (x >= p.a[lo].nx || y >= p.a[lo].ny) return;
+    node_step<S, ODD, GENERAL, GMODE>(p.a[lo], x, y);
+}
+
+}  // namespace trt

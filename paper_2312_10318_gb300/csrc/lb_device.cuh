@@ -223,16 +223,13 @@ __device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, 
 
 // ---- kernels ----------------------------------------------------------------
 
-// One fused AA step (pull-stream, moments, regularized TRT collision, G_i,
-// F_i, push-back into the same slots, half-way bounce-back) for every fluid
-// node; one thread per node.  GENERAL enables walls, masks and non-periodic
-// edges; GMODE is G_LAGGED or G_OFF.
+// One fused AA step of one node (pull-stream, moments, regularized TRT
+// collision, G_i, F_i, push-back into the same slots, half-way bounce-back);
+// non-fluid nodes return at once.  GENERAL enables walls, masks and
+// non-periodic edges; GMODE is G_LAGGED or G_OFF.
 template <typename S, bool ODD, bool GENERAL, int GMODE>
-__global__ void __launch_bounds__(256) k_step(Args<typename Fmt<S>::C> a) {
+__device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int x, int y) {
     using C = typename Fmt<S>::C;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
     S* __restrict__ F = static_cast<S*>(a.f);
     const long long own = (long long)y * a.pitch + x;
     if (GENERAL && a.mask && a.mask[own] != FLUID) return;
@@ -273,6 +270,14 @@ __global__ void __launch_bounds__(256) k_step(Args<typename Fmt<S>::C> a) {
             dst = (long long)i * a.plane + nb[i];
         F[dst] = Fmt<S>::st(v);
     }
+}
+
+template <typename S, bool ODD, bool GENERAL, int GMODE>
+__global__ void __launch_bounds__(256) k_step(Args<typename Fmt<S>::C> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    node_step<S, ODD, GENERAL, GMODE>(a, x, y);
 }
 
 // Outlet ghosts, after a step that produced a state of parity ODD_NEW: every

@@ -1,0 +1,25 @@
+// Internal layout of a lattice handle, shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb_ops.cuh"
+#include "trtrlb.h"
+
+struct trtrlb_lattice {
+    trtrlb_params p;
+    trt::State s;
+    cudaStream_t stream;
+    int64_t t;           // steps since init / set_f
+    void* f;             // device allocations owned by the handle
+    void* phi;           // both Phi buffers in one allocation
+    uint8_t* mask;
+    int* ghosts;
+    double* stage;       // FP64 staging for host transfers, 11 * n
+    double* part;        // diagnostics partials (scratch)
+    double* dout;        // diagnostics result, 8 doubles
+    int64_t bytes;
+    int tile_w;          // batched-kernel tile width (32, 64, 128 or 256 nodes)
+    char err[256];
+};
+

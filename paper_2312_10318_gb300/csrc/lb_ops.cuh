@@ -39,6 +39,15 @@ template <typename S> struct Ops {
     static cudaError_t set_f(State& s, const double* f, const double* phi, cudaStream_t st);
     // Deterministic FP64 diagnostics; part holds diag_blocks() * 8 doubles.
     static cudaError_t diagnostics(const State& s, double* part, double* out, cudaStream_t st);
+    // One batched step of n lattices that share the boundary flavour
+    // (general), G mode and the parity of their current level (odd); cur[q]
+    // is the Phi buffer holding member q's previous level, log2_tw[q] its tile
+    // width.  Launches ceil(n / 64) kernels.
+    static cudaError_t step_group(const State* const* members, const int* cur, const int* log2_tw,
+                                  int n, bool odd, bool general, int g_mode, cudaStream_t st);
+    // Outlet-ghost pass after step index k of a sequence that started at the
+    // state's current parity and Phi buffer.
+    static cudaError_t ghost_pass(const State& s, int k, cudaStream_t st);
 };
 
 int diag_blocks(const State& s);

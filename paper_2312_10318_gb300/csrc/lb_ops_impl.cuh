@@ -1,6 +1,7 @@
 // Definitions of Ops<S> (lb_ops.cuh); included once per storage format.
 #pragma once
 #include "lb_aux.cuh"
+#include "lb_batch.cuh"
 #include "lb_ops.cuh"
 
 namespace trt {
@@ -143,6 +144,71 @@ cudaError_t Ops<S>::diagnostics(const State& s, double* part, double* out, cudaS
     if (s.parity) k_diag_partial<S, true><<<nb, DIAG_THREADS, 0, st>>>(a, part);
     else k_diag_partial<S, false><<<nb, DIAG_THREADS, 0, st>>>(a, part);
     k_diag_final<<<1, DIAG_THREADS, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+template <typename S, bool ODD, bool GENERAL, int GMODE, int MAXL>
+static cudaError_t launch_group(const State* const* m, const int* cur, const int* l2tw, int n,
+                                cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    GroupParams<C, MAXL> p;
+    p.n = n;
+    int tiles = 0;
+    for (int q = 0; q < n; ++q) {
+        State v = *m[q];
+        v.cur = cur[q];
+        p.a[q] = make_args<C>(v);
+        const int tw = 1 << l2tw[q], th = BATCH_THREADS / tw;
+        p.log2_tw[q] = l2tw[q];
+        p.tiles_x[q] = (v.nx + tw - 1) / tw;
+        p.tile_begin[q] = tiles;
+        tiles += p.tiles_x[q] * ((v.ny + th - 1) / th);
+    }
+    p.tile_begin[n] = tiles;
+    k_step_group<S, ODD, GENERAL, GMODE, MAXL><<<tiles, BATCH_THREADS, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S, bool ODD, bool GENERAL, int GMODE>
+static cudaError_t launch_group_sized(const State* const* m, const int* cur, const int* l2tw,
+                                      int n, cudaStream_t st) {
+    for (int q0 = 0; q0 < n; q0 += 64) {
+        const int c = n - q0 < 64 ? n - q0 : 64;
+        const cudaError_t e = c <= 4
+            ? launch_group<S, ODD, GENERAL, GMODE, 4>(m + q0, cur + q0, l2tw + q0, c, st)
+            : launch_group<S, ODD, GENERAL, GMODE, 64>(m + q0, cur + q0, l2tw + q0, c, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename S>
+cudaError_t Ops<S>::step_group(const State* const* m, const int* cur, const int* l2tw, int n,
+                               bool odd, bool general, int g_mode, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const bool off = g_mode == G_OFF;
+#define TRT_G(O, G)                                                                   \
+    return off ? launch_group_sized<S, O, G, G_OFF>(m, cur, l2tw, n, st)             \
+               : launch_group_sized<S, O, G, G_LAGGED>(m, cur, l2tw, n, st);
+    if (odd) {
+        if (general) { TRT_G(true, true) } else { TRT_G(true, false) }
+    } else {
+        if (general) { TRT_G(false, true) } else { TRT_G(false, false) }
+    }
+#undef TRT_G
+}
+
+template <typename S>
+cudaError_t Ops<S>::ghost_pass(const State& s, int k, cudaStream_t st) {
+    if (s.nghost <= 0) return cudaSuccess;
+    using C = typename Fmt<S>::C;
+    State v = s;
+    v.parity = s.parity ^ (k & 1);
+    if (s.g_mode == G_LAGGED) v.cur = s.cur ^ (k & 1);
+    const Args<C> a = make_args<C>(v);
+    const int t = 128, g = (s.nghost + t - 1) / t;
+    if (v.parity == 0) k_ghosts<S, true><<<g, t, 0, st>>>(a, s.ghosts, s.nghost);
+    else k_ghosts<S, false><<<g, t, 0, st>>>(a, s.ghosts, s.nghost);
     return cudaGetLastError();
 }
 

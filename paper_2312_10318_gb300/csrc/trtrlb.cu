@@ -12,24 +12,8 @@
 #include <new>
 #include <vector>
 
-#include "lb_ops.cuh"
-#include "trtrlb.h"
+#include "lb_handle.h"
 
-struct trtrlb_lattice {
-    trtrlb_params p;
-    trt::State s;
-    cudaStream_t stream;
-    int64_t t;           // steps since init / set_f
-    void* f;             // device allocations owned by the handle
-    void* phi;           // both Phi buffers in one allocation
-    uint8_t* mask;
-    int* ghosts;
-    double* stage;       // FP64 staging for host transfers, 11 * n
-    double* part;        // diagnostics partials (scratch)
-    double* dout;        // diagnostics result, 8 doubles
-    int64_t bytes;
-    char err[256];
-};
 
 namespace {
 
@@ -241,6 +225,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         return rc;
     }
     h->t = 0;
+    h->tile_w = p.nx >= 128 ? 128 : (p.nx >= 64 ? 64 : 32);
     *out = h;
     return TRTRLB_OK;
 }
