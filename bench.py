@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,25 +40,42 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 PHI_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4}
 
 
-def workload(name: str):
-    """(problems, storage, description) of a named workload."""
+def workload(name: str, size=None, storage=None):
+    """(problems, storage, description) of a named workload; size "NXxNY" and
+    storage override the defaults (for profiling runs)."""
     from paper_2312_10318_gb300 import workloads as W
     if name == "dsl1024":
         res = (1e4, 1e5, 1e7)
-        probs = [W.double_shear_layer(1024, re=r) for r in res]
-        desc = ("double shear layer, 3 lattices 1024x1024 periodic (Re 1e4, 1e5, 1e7), kappa=80, "
-                "delta=0.05, u_c=0.04, tau_s2=0.625, FP32 storage, G lagged")
-        return probs, "f32", desc
+        n = 1024
+        nx, ny = (n, n) if size is None else size
+        probs = [W.double_shear_layer(nx, re=r) for r in res]
+        if size is not None:
+            probs = [_rect(p, nx, ny) for p in probs]
+        st = storage or "f32"
+        desc = (f"double shear layer, 3 lattices {nx}x{ny} periodic (Re 1e4, 1e5, 1e7), kappa=80, "
+                f"delta=0.05, u_c=0.04, tau_s2=0.625, {st.upper()} storage, G lagged")
+        return probs, st, desc
     if name == "dsl4096":
-        probs = [W.double_shear_layer(4096, re=1e5)]
-        return probs, "f32", "double shear layer, 1 lattice 4096x4096 periodic, Re 1e5, FP32 storage, G lagged"
-    if name == "dsl4096_f16":
-        probs = [W.double_shear_layer(4096, re=1e5)]
-        return probs, "f16", "double shear layer, 1 lattice 4096x4096 periodic, Re 1e5, FP16-shifted storage, G lagged"
+        nx, ny = (4096, 4096) if size is None else size
+        p = W.double_shear_layer(nx, re=1e5)
+        if size is not None:
+            p = _rect(p, nx, ny)
+        st = storage or "f32"
+        return [p], st, f"double shear layer, 1 lattice {nx}x{ny} periodic, Re 1e5, {st.upper()} storage, G lagged"
     if name == "tg64":
         probs = [W.taylor_green(64, 0.04, 100.0, magic=0.25)]
-        return probs, "f64", "Taylor-Green 64x64 periodic, u0=0.04, Re=100, magic 1/4, FP64"
+        st = storage or "f64"
+        return probs, st, f"Taylor-Green 64x64 periodic, u0=0.04, Re=100, magic 1/4, {st.upper()}"
     raise SystemExit(f"unknown workload {name}")
+
+
+def _rect(p, nx, ny):
+    """The problem's parameters on an nx x ny lattice (fields cut or tiled)."""
+    reps = (-(-ny // p.ny), -(-nx // p.nx))
+    p.ux = np.tile(p.ux, reps)[:ny, :nx].copy()
+    p.uy = np.tile(p.uy, reps)[:ny, :nx].copy()
+    p.nx, p.ny = nx, ny
+    return p
 
 
 def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
@@ -240,16 +259,23 @@ def main():
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--e2e-steps", type=int, default=100, help="time steps per end-to-end solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=None, help="override the lattice size, NXxNY")
+    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "vector"])
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="batch", choices=["batch", "single"],
                     help="batch: one launch per time step for all lattices; single: one per lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    problems, storage, desc = workload(args.workload)
+    size = None
+    if args.size:
+        nx_s, ny_s = args.size.lower().split("x")
+        size = (int(nx_s), int(ny_s))
+    problems, storage, desc = workload(args.workload, size, args.storage)
     if args.impl == "reference":
         return run_reference(args, problems, desc)
 
-    import numpy as np
     import torch
     from paper_2312_10318_gb300 import Lattice
     from paper_2312_10318_gb300.lattice import Batch
@@ -274,6 +300,7 @@ def main():
     for pr in problems:
         lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode="lagged", stream=stream,
                       **pr.lattice_kwargs())
+        lat.set_kernel(args.kernel)
         lat.init(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
                    for a in (pr.ux, pr.uy, pr.rho)))
         lats.append(lat)
@@ -341,7 +368,7 @@ def main():
                 for a in (p.ux, p.uy, p.rho)] for p in problems]
     host_out = [[torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(3)] for p in problems]
     e2e_times = []
-    for rep in range(3):
+    for rep in range(0 if args.no_e2e else 3):
         barrier()
         t0 = time.perf_counter()
         for lat, (ux, uy, rho) in zip(lats, host_in):
@@ -351,7 +378,7 @@ def main():
             lat.moments(*out)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = statistics.median(e2e_times)
+    e2e_t = statistics.median(e2e_times) if e2e_times else float("nan")
     if dist is not None:
         t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -366,7 +393,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
             "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
                        "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
-                       "g_mode": "lagged", "parallelism": f"replicas x{world}",
+                       "g_mode": "lagged", "kernel": [l.kernel()[0] and "vector" or "scalar" for l in lats][0],
+                       "parallelism": f"replicas x{world}",
                        "launch": "one batched kernel per time step" if args.mode == "batch"
                                  else "one kernel per lattice and time step",
                        "l2": f"{args.flush_mib} MiB written then read before every timed step "

@@ -176,6 +176,22 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
                                int32_t periodic_x, int32_t periodic_y, double gx, double gy,
                                double* out, void* stream);
 
+/* Kernel shape of a lattice's step (the autotuner's knobs; results do not
+ * depend on them).  variant: TRTRLB_KERNEL_AUTO (vector kernel whenever it
+ * applies), TRTRLB_KERNEL_SCALAR (one node per thread), TRTRLB_KERNEL_VECTOR
+ * (16-byte vectors of nodes per thread; ENOTSUP unless the lattice is periodic
+ * in both directions, has no mask and nx is a multiple of 16 / element size).
+ * tile_w: width in nodes of the scalar kernel's 256-thread tile in batches
+ * (32, 64, 128 or 256; 0 keeps the current one). */
+#define TRTRLB_KERNEL_AUTO 0
+#define TRTRLB_KERNEL_SCALAR 1
+#define TRTRLB_KERNEL_VECTOR 2
+int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w);
+
+/* The kernel in use: *vector = 1 for the vector kernel; *tile_w as above.
+ * Either pointer may be NULL. */
+int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w);
+
 /* ---- batches ---------------------------------------------------------------
  * A batch advances several lattices together: per time step one kernel launch
  * per storage format covers every tile of every lattice in the batch (the

@@ -15,6 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5,
 F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR = 0, 1, 2
 
 # every function the header declares, with (restype, argtypes)
 _vp, _dp, _i64 = C.c_void_p, C.c_void_p, C.c_int64
@@ -48,6 +49,8 @@ SIGNATURES = {
     "trtrlb_diagnostics_noalloc": (C.c_int, [_dp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_double, C.c_double, _dp, _vp]),
     "trtrlb_device_bytes": (C.c_int64, [_vp]),
+    "trtrlb_set_kernel": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "trtrlb_get_kernel": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "trtrlb_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "trtrlb_batch_set": (C.c_int, [_vp, C.POINTER(_vp), C.c_int]),
     "trtrlb_batch_step": (C.c_int, [_vp, _i64]),

@@ -77,13 +77,14 @@ int log2i(int v) {
 // Launches n steps of every member, starting from the members' current
 // states; step q sees parity ^ (q & 1) and, for lagged G, cur ^ (q & 1).
 cudaError_t launch_steps(trtrlb_batch* b, int64_t n) {
-    using Key = std::tuple<int, int, int, int>;  // storage, general, g_mode, odd
+    using Key = std::tuple<int, int, int, int>;  // storage, flavour, g_mode, odd
     for (int64_t q = 0; q < n; ++q) {
         const int flip = (int)(q & 1);
         std::map<Key, std::vector<int>> groups;
         for (int i = 0; i < (int)b->lats.size(); ++i) {
             const trtrlb_lattice* h = b->lats[i];
-            groups[Key{h->p.storage, h->s.general ? 1 : 0, h->s.g_mode, h->s.parity ^ flip}].push_back(i);
+            const int flav = h->s.general ? trt::FLAV_GENERAL : (h->s.vec ? trt::FLAV_VECTOR : trt::FLAV_PERIODIC);
+            groups[Key{h->p.storage, flav, h->s.g_mode, h->s.parity ^ flip}].push_back(i);
         }
         for (const auto& kv : groups) {
             const Key& k = kv.first;
@@ -97,7 +98,7 @@ cudaError_t launch_steps(trtrlb_batch* b, int64_t n) {
             }
             const cudaError_t e = TRT_DISPATCH_S(
                 std::get<0>(k), step_group(m.data(), cur.data(), l2.data(), (int)m.size(),
-                                           std::get<3>(k) != 0, std::get<1>(k) != 0,
+                                           std::get<3>(k) != 0, std::get<1>(k),
                                            std::get<2>(k), b->stream));
             if (e != cudaSuccess) return e;
         }

@@ -5,6 +5,7 @@
 // loads; the per-node body is the fully specialised node_step.
 #pragma once
 #include "lb_device.cuh"
+#include "lb_vec.cuh"
 
 namespace trt {
 
@@ -14,7 +15,8 @@ template <typename C, int MAXL> struct GroupParams {
     int n;                       // lattices in this launch
     int tile_begin[MAXL + 1];    // prefix sums of tiles; tile_begin[n] = total
     int tiles_x[MAXL];           // tiles per tile row
-    int log2_tw[MAXL];           // tile width 2^log2_tw nodes, height 256 / width
+    int log2_tw[MAXL];           // scalar: tile width 2^log2_tw nodes, height 256 / width
+    int segs[MAXL];              // vector: warp segments per row
     Args<C> a[MAXL];
 };
 
@@ -35,6 +37,27 @@ __global__ void __launch_bounds__(BATCH_THREADS)
     const int y = (ty << (8 - lt)) + ((int)threadIdx.x >> lt);
     if (x >= p.a[lo].nx || y >= p.a[lo].ny) return;
     node_step<S, ODD, GENERAL, GMODE>(p.a[lo], x, y);
+}
+
+// Vectorised flavour: a CTA owns 8 consecutive warp segments of one lattice.
+template <typename S, bool ODD, int GMODE, int MAXL>
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_step_group_vec(const __grid_constant__ GroupParams<typename Fmt<S>::C, MAXL> p) {
+    constexpr int V = Pk<S>::V;
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = p.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tile_begin[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int lane = (int)threadIdx.x & 31;
+    const long long s = (long long)(b - p.tile_begin[lo]) * 8 + ((int)threadIdx.x >> 5);
+    const int spr = p.segs[lo];
+    if (s >= (long long)spr * p.a[lo].ny) return;   // whole warp leaves together
+    const int y = (int)(s / spr);
+    const int x0 = (int)(s % spr) * 32 * V + lane * V;
+    seg_step<S, ODD, GMODE>(p.a[lo], x0, y, lane);
 }
 
 }  // namespace trt

@@ -19,7 +19,8 @@ struct trtrlb_lattice {
     double* part;        // diagnostics partials (scratch)
     double* dout;        // diagnostics result, 8 doubles
     int64_t bytes;
-    int tile_w;          // batched-kernel tile width (32, 64, 128 or 256 nodes)
+    int tile_w;          // scalar-kernel tile width in the batched path (32 .. 256 nodes)
+    int variant;         // TRTRLB_KERNEL_AUTO / SCALAR / VECTOR
     char err[256];
 };
 

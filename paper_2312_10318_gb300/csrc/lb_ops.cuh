@@ -9,6 +9,12 @@ namespace trt {
 // Threads per block of the diagnostics reduction.
 constexpr int DIAG_THREADS = 256;
 
+// Kernel flavours of a lattice's step.
+enum : int { FLAV_GENERAL = 0, FLAV_PERIODIC = 1, FLAV_VECTOR = 2 };
+
+// Nodes per thread of the vectorised kernel (16 bytes of storage).
+inline int vec_width(int storage_bytes) { return 16 / storage_bytes; }
+
 // Format-independent description of a lattice's device state.
 struct State {
     void* f;              // populations, S[9][ny][pitch]
@@ -21,6 +27,7 @@ struct State {
     long long plane;
     int px, py;
     bool general;         // walls, mask or non-periodic edges present
+    bool vec;             // the 128-bit vectorised kernel runs this lattice
     int g_mode;
     double tau1, tau2, gx, gy, rho0;
     double wall_ux, wall_uy, wall_rho;
@@ -39,12 +46,12 @@ template <typename S> struct Ops {
     static cudaError_t set_f(State& s, const double* f, const double* phi, cudaStream_t st);
     // Deterministic FP64 diagnostics; part holds diag_blocks() * 8 doubles.
     static cudaError_t diagnostics(const State& s, double* part, double* out, cudaStream_t st);
-    // One batched step of n lattices that share the boundary flavour
-    // (general), G mode and the parity of their current level (odd); cur[q]
-    // is the Phi buffer holding member q's previous level, log2_tw[q] its tile
-    // width.  Launches ceil(n / 64) kernels.
+    // One batched step of n lattices that share the kernel flavour (FLAV_*),
+    // G mode and the parity of their current level (odd); cur[q] is the Phi
+    // buffer holding member q's previous level, log2_tw[q] its tile width
+    // (scalar flavours).  Launches ceil(n / 64) kernels.
     static cudaError_t step_group(const State* const* members, const int* cur, const int* log2_tw,
-                                  int n, bool odd, bool general, int g_mode, cudaStream_t st);
+                                  int n, bool odd, int flavour, int g_mode, cudaStream_t st);
     // Outlet-ghost pass after step index k of a sequence that started at the
     // state's current parity and Phi buffer.
     static cudaError_t ghost_pass(const State& s, int k, cudaStream_t st);

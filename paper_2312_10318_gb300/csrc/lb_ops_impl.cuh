@@ -46,12 +46,28 @@ static void launch_step(const State& s, const Args<typename Fmt<S>::C>& a, cudaS
     }
 }
 
+template <typename S, bool ODD>
+static void launch_step_vec(const State& s, const Args<typename Fmt<S>::C>& a, cudaStream_t st) {
+    constexpr int V = Pk<S>::V;
+    const int spr = (s.nx + 32 * V - 1) / (32 * V);
+    const long long nseg = (long long)spr * s.ny;
+    const int blocks = (int)((nseg + 7) / 8);
+    if (s.g_mode == G_OFF) k_step_vec<S, ODD, G_OFF><<<blocks, 256, 0, st>>>(a, spr);
+    else k_step_vec<S, ODD, G_LAGGED><<<blocks, 256, 0, st>>>(a, spr);
+}
+
 template <typename S>
 cudaError_t Ops<S>::step(State& s, cudaStream_t st) {
     using C = typename Fmt<S>::C;
     const Args<C> a = make_args<C>(s);
-    if (s.parity == 0) launch_step<S, false>(s, a, st);
-    else launch_step<S, true>(s, a, st);
+    if (s.vec) {
+        if (s.parity == 0) launch_step_vec<S, false>(s, a, st);
+        else launch_step_vec<S, true>(s, a, st);
+    } else if (s.parity == 0) {
+        launch_step<S, false>(s, a, st);
+    } else {
+        launch_step<S, true>(s, a, st);
+    }
     if (s.nghost > 0) {
         const int t = 128, g = (s.nghost + t - 1) / t;
         if (s.parity == 0) k_ghosts<S, true><<<g, t, 0, st>>>(a, s.ghosts, s.nghost);
@@ -147,10 +163,12 @@ cudaError_t Ops<S>::diagnostics(const State& s, double* part, double* out, cudaS
     return cudaGetLastError();
 }
 
-template <typename S, bool ODD, bool GENERAL, int GMODE, int MAXL>
+// FLAV: FLAV_GENERAL, FLAV_PERIODIC (scalar kernels) or FLAV_VECTOR.
+template <typename S, bool ODD, int FLAV, int GMODE, int MAXL>
 static cudaError_t launch_group(const State* const* m, const int* cur, const int* l2tw, int n,
                                 cudaStream_t st) {
     using C = typename Fmt<S>::C;
+    constexpr int V = Pk<S>::V;
     GroupParams<C, MAXL> p;
     p.n = n;
     int tiles = 0;
@@ -158,44 +176,60 @@ static cudaError_t launch_group(const State* const* m, const int* cur, const int
         State v = *m[q];
         v.cur = cur[q];
         p.a[q] = make_args<C>(v);
-        const int tw = 1 << l2tw[q], th = BATCH_THREADS / tw;
-        p.log2_tw[q] = l2tw[q];
-        p.tiles_x[q] = (v.nx + tw - 1) / tw;
         p.tile_begin[q] = tiles;
-        tiles += p.tiles_x[q] * ((v.ny + th - 1) / th);
+        if (FLAV == FLAV_VECTOR) {
+            p.segs[q] = (v.nx + 32 * V - 1) / (32 * V);
+            p.tiles_x[q] = 0;
+            p.log2_tw[q] = 0;
+            tiles += (int)(((long long)p.segs[q] * v.ny + 7) / 8);
+        } else {
+            const int tw = 1 << l2tw[q], th = BATCH_THREADS / tw;
+            p.log2_tw[q] = l2tw[q];
+            p.segs[q] = 0;
+            p.tiles_x[q] = (v.nx + tw - 1) / tw;
+            tiles += p.tiles_x[q] * ((v.ny + th - 1) / th);
+        }
     }
     p.tile_begin[n] = tiles;
-    k_step_group<S, ODD, GENERAL, GMODE, MAXL><<<tiles, BATCH_THREADS, 0, st>>>(p);
+    if (FLAV == FLAV_VECTOR)
+        k_step_group_vec<S, ODD, GMODE, MAXL><<<tiles, BATCH_THREADS, 0, st>>>(p);
+    else
+        k_step_group<S, ODD, FLAV == FLAV_GENERAL, GMODE, MAXL><<<tiles, BATCH_THREADS, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename S, bool ODD, bool GENERAL, int GMODE>
+template <typename S, bool ODD, int FLAV, int GMODE>
 static cudaError_t launch_group_sized(const State* const* m, const int* cur, const int* l2tw,
                                       int n, cudaStream_t st) {
     for (int q0 = 0; q0 < n; q0 += 64) {
         const int c = n - q0 < 64 ? n - q0 : 64;
         const cudaError_t e = c <= 4
-            ? launch_group<S, ODD, GENERAL, GMODE, 4>(m + q0, cur + q0, l2tw + q0, c, st)
-            : launch_group<S, ODD, GENERAL, GMODE, 64>(m + q0, cur + q0, l2tw + q0, c, st);
+            ? launch_group<S, ODD, FLAV, GMODE, 4>(m + q0, cur + q0, l2tw + q0, c, st)
+            : launch_group<S, ODD, FLAV, GMODE, 64>(m + q0, cur + q0, l2tw + q0, c, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+template <typename S, bool ODD, int FLAV>
+static cudaError_t launch_group_g(const State* const* m, const int* cur, const int* l2tw, int n,
+                                  int g_mode, cudaStream_t st) {
+    return g_mode == G_OFF ? launch_group_sized<S, ODD, FLAV, G_OFF>(m, cur, l2tw, n, st)
+                           : launch_group_sized<S, ODD, FLAV, G_LAGGED>(m, cur, l2tw, n, st);
+}
+
 template <typename S>
 cudaError_t Ops<S>::step_group(const State* const* m, const int* cur, const int* l2tw, int n,
-                               bool odd, bool general, int g_mode, cudaStream_t st) {
+                               bool odd, int flavour, int g_mode, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const bool off = g_mode == G_OFF;
-#define TRT_G(O, G)                                                                   \
-    return off ? launch_group_sized<S, O, G, G_OFF>(m, cur, l2tw, n, st)             \
-               : launch_group_sized<S, O, G, G_LAGGED>(m, cur, l2tw, n, st);
     if (odd) {
-        if (general) { TRT_G(true, true) } else { TRT_G(true, false) }
-    } else {
-        if (general) { TRT_G(false, true) } else { TRT_G(false, false) }
+        if (flavour == FLAV_GENERAL) return launch_group_g<S, true, FLAV_GENERAL>(m, cur, l2tw, n, g_mode, st);
+        if (flavour == FLAV_VECTOR) return launch_group_g<S, true, FLAV_VECTOR>(m, cur, l2tw, n, g_mode, st);
+        return launch_group_g<S, true, FLAV_PERIODIC>(m, cur, l2tw, n, g_mode, st);
     }
-#undef TRT_G
+    if (flavour == FLAV_GENERAL) return launch_group_g<S, false, FLAV_GENERAL>(m, cur, l2tw, n, g_mode, st);
+    if (flavour == FLAV_VECTOR) return launch_group_g<S, false, FLAV_VECTOR>(m, cur, l2tw, n, g_mode, st);
+    return launch_group_g<S, false, FLAV_PERIODIC>(m, cur, l2tw, n, g_mode, st);
 }
 
 template <typename S>

@@ -226,6 +226,8 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     }
     h->t = 0;
     h->tile_w = p.nx >= 128 ? 128 : (p.nx >= 64 ? 64 : 32);
+    h->variant = TRTRLB_KERNEL_AUTO;
+    s.vec = !s.general && p.nx % trt::vec_width((int)es) == 0;
     *out = h;
     return TRTRLB_OK;
 }
@@ -359,6 +361,37 @@ int trtrlb_diagnostics(trtrlb_t h, double* out) {
 }
 
 int64_t trtrlb_device_bytes(trtrlb_t h) { return h ? h->bytes : -1; }
+
+int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (tile_w != 0 && tile_w != 32 && tile_w != 64 && tile_w != 128 && tile_w != 256)
+        return fail(h->err, TRTRLB_EINVAL, "tile_w must be 0, 32, 64, 128 or 256");
+    const bool can_vec = !h->s.general && h->p.nx % trt::vec_width((int)elem_size(h->p.storage)) == 0;
+    bool vec;
+    switch (variant) {
+        case TRTRLB_KERNEL_AUTO: vec = can_vec; break;
+        case TRTRLB_KERNEL_SCALAR: vec = false; break;
+        case TRTRLB_KERNEL_VECTOR:
+            if (!can_vec)
+                return fail(h->err, TRTRLB_ENOTSUP,
+                            "the vector kernel needs a periodic lattice without mask and nx divisible by its width");
+            vec = true;
+            break;
+        default: return fail(h->err, TRTRLB_EINVAL, "unknown kernel variant");
+    }
+    h->variant = variant;
+    h->s.vec = vec;
+    if (tile_w) h->tile_w = tile_w;
+    return TRTRLB_OK;
+}
+
+int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w) {
+    if (!h) return TRTRLB_EINVAL;
+    if (vector) *vector = h->s.vec ? 1 : 0;
+    if (tile_w) *tile_w = h->tile_w;
+    return TRTRLB_OK;
+}
 
 const char* trtrlb_strerror(int code) {
     switch (code) {

@@ -136,6 +136,18 @@ class Lattice:
         s = stream if isinstance(stream, int) else stream.cuda_stream
         self._chk(self._lib.trtrlb_set_stream(self._h, C.c_void_p(s)))
 
+    def set_kernel(self, variant="auto", tile_w=0):
+        """Kernel shape: 'auto' | 'scalar' | 'vector', scalar tile width (0 keeps it)."""
+        v = {"auto": _lib.KERNEL_AUTO, "scalar": _lib.KERNEL_SCALAR, "vector": _lib.KERNEL_VECTOR}[variant]
+        self._chk(self._lib.trtrlb_set_kernel(self._h, v, int(tile_w)))
+        return self
+
+    def kernel(self):
+        """(vector kernel in use, scalar tile width)."""
+        vec, tw = C.c_int32(), C.c_int32()
+        self._chk(self._lib.trtrlb_get_kernel(self._h, C.byref(vec), C.byref(tw)))
+        return bool(vec.value), tw.value
+
     def init(self, ux, uy, rho=None):
         """Initial state from (rho, u) (rho None: rho0)."""
         sh = self.shape
