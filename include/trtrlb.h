@@ -179,8 +179,9 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
 /* Kernel shape of a lattice's step (the autotuner's knobs; results do not
  * depend on them).  variant: TRTRLB_KERNEL_AUTO (vector kernel whenever it
  * applies), TRTRLB_KERNEL_SCALAR (one node per thread), TRTRLB_KERNEL_VECTOR
- * (16-byte vectors of nodes per thread; ENOTSUP unless the lattice is periodic
- * in both directions, has no mask and nx is a multiple of 16 / element size).
+ * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
+ * lattice is periodic in both directions, has no mask and nx is a multiple
+ * of that width).
  * tile_w: width in nodes of the scalar kernel's 256-thread tile in batches
  * (32, 64, 128 or 256; 0 keeps the current one). */
 #define TRTRLB_KERNEL_AUTO 0

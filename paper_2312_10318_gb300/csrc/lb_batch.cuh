@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(BATCH_THREADS)
 
 // Vectorised flavour: a CTA owns 8 consecutive warp segments of one lattice.
 template <typename S, bool ODD, int GMODE, int MAXL>
-__global__ void __launch_bounds__(BATCH_THREADS)
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(S) == 2 ? 4 : 3)
     k_step_group_vec(const __grid_constant__ GroupParams<typename Fmt<S>::C, MAXL> p) {
     constexpr int V = Pk<S>::V;
     const int b = (int)blockIdx.x;

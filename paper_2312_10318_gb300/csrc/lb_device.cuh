@@ -151,21 +151,28 @@ __device__ __forceinline__ long long pop_loc(long long plane, const long long (&
 //   a3_xxy = rho u_x^2 u_y + (1 - 1/tau2) A_xxy  (and xyy alike),
 // f*_i = w_i [rho + 3 e_i.a1 + 9/2 H_i,ab a2_ab + 27/2 (H_i,xxy a3_xxy +
 // H_i,xyy a3_xyy)], because 1/(2 c_s^4) = 1/(6 c_s^6) = 9/2, H_xxx = H_yyy = 0
-// and the first-order terms of eq2 combine into w_i e_i.(j + F)/c_s^2.
-// Returns rho and u (eq11, with the half-force shift).
+// and the first-order terms of eq2 combine into w_i e_i.(j + F)/c_s^2.  The
+// weights w_i are folded into the coefficients below.  The raw moments share
+// their partial sums (the compiler may not reassociate float additions).
+// Returns Phi_xxx = rho u_x^3 and Phi_yyy = rho u_y^3 of the node (eq11 u).
 template <typename C>
 __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k2,
                                         const C kf, const C gx, const C gy, const C rho0,
-                                        C (&o)[9], C& rho_o, C& ux_o, C& uy_o) {
+                                        C (&o)[9], C& phx, C& phy) {
     const C third = C(1) / C(3);
-    const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const C jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    const C sxx = (d[1] + d[3]) + (d[5] + d[6]) + (d[7] + d[8]);
-    const C syy = (d[2] + d[4]) + (d[5] + d[6]) + (d[7] + d[8]);
-    const C pxy = (d[5] + d[7]) - (d[6] + d[8]);
-    const C qxxy = (d[5] + d[6]) - (d[7] + d[8]);
-    const C qxyy = (d[5] + d[8]) - (d[6] + d[7]);
+    // raw moments of the shifted populations
+    const C s13 = d[1] + d[3], m13 = d[1] - d[3];
+    const C s24 = d[2] + d[4], m24 = d[2] - d[4];
+    const C a57 = d[5] + d[7], m57 = d[5] - d[7];
+    const C a68 = d[6] + d[8], m68 = d[6] - d[8];
+    const C sd = a57 + a68;      // sum of the four diagonal populations
+    const C pxy = a57 - a68;     // sum e_x e_y d
+    const C qxxy = m57 + m68;    // sum e_x^2 e_y d
+    const C qxyy = m57 - m68;    // sum e_x e_y^2 d
+    const C jx = m13 + qxyy;     // sum e_x d
+    const C jy = m24 + qxxy;     // sum e_y d
+    const C drho = (d[0] + sd) + (s13 + s24);
+    // eq11: rho = sum f, u = (sum e f)/rho + g/2
     const C rho = rho0 + drho;
     const C inv = C(1) / rho;
     const C ux = jx * inv + C(0.5) * gx;
@@ -173,39 +180,43 @@ __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k
     const C Fx = rho * gx, Fy = rho * gy;
     const C rux = rho * ux, ruy = rho * uy;
     const C ruxx = rux * ux, ruyy = ruy * uy, ruxy = rux * uy;
+    const C rxxy = ruxx * uy, rxyy = ruyy * ux;
     // eq9 with the equilibrium moments of eq9_2 (A_x = -F_x/2 is folded into a1)
-    const C Axx = sxx - third * drho - ruxx;
-    const C Ayy = syy - third * drho - ruyy;
+    const C drho3 = third * drho;
+    const C Axx = (s13 + sd) - drho3 - ruxx;
+    const C Ayy = (s24 + sd) - drho3 - ruyy;
     const C Axy = pxy - ruxy;
-    const C Axxy = qxxy - third * jy - ruxx * uy;
-    const C Axyy = qxyy - third * jx - ruyy * ux;
+    const C Axxy = qxxy - third * jy - rxxy;
+    const C Axyy = qxyy - third * jx - rxyy;
     const C a1x = jx + Fx, a1y = jy + Fy;
     const C a2xx = ruxx + k1 * Axx + kf * (C(2) * Fx * ux - dpx);
     const C a2yy = ruyy + k1 * Ayy + kf * (C(2) * Fy * uy - dpy);
     const C a2xy = ruxy + k1 * Axy + kf * (Fx * uy + ux * Fy);
-    const C a3xxy = ruxx * uy + k2 * Axxy;
-    const C a3xyy = ruyy * ux + k2 * Axyy;
-    const C c13 = drho + C(3) * a2xx - C(1.5) * a2yy;
-    const C o13 = C(3) * a1x - C(4.5) * a3xyy;
-    const C c24 = drho - C(1.5) * a2xx + C(3) * a2yy;
-    const C o24 = C(3) * a1y - C(4.5) * a3xxy;
-    const C cd = drho + C(3) * (a2xx + a2yy);
-    const C c57 = cd + C(9) * a2xy, c68 = cd - C(9) * a2xy;
-    const C o57 = C(3) * (a1x + a1y) + C(9) * (a3xxy + a3xyy);
-    const C o68 = C(3) * (a1y - a1x) + C(9) * (a3xxy - a3xyy);
-    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
-    o[0] = w0 * (drho - C(1.5) * (a2xx + a2yy));
-    o[1] = w1 * (c13 + o13);
-    o[3] = w1 * (c13 - o13);
-    o[2] = w1 * (c24 + o24);
-    o[4] = w1 * (c24 - o24);
-    o[5] = w5 * (c57 + o57);
-    o[7] = w5 * (c57 - o57);
-    o[6] = w5 * (c68 + o68);
-    o[8] = w5 * (c68 - o68);
-    rho_o = rho;
-    ux_o = ux;
-    uy_o = uy;
+    const C a3xxy = rxxy + k2 * Axxy;
+    const C a3xyy = rxyy + k2 * Axyy;
+    // reconstruction, w_i folded in: w0 = 4/9, w1..4 = 1/9, w5..8 = 1/36
+    const C t = a2xx + a2yy;
+    o[0] = C(4.0 / 9.0) * drho - C(2.0 / 3.0) * t;
+    const C b9 = C(1.0 / 9.0) * drho;
+    const C c13 = b9 + C(1.0 / 3.0) * a2xx - C(1.0 / 6.0) * a2yy;
+    const C o13 = C(1.0 / 3.0) * a1x - C(0.5) * a3xyy;
+    const C c24 = b9 - C(1.0 / 6.0) * a2xx + C(1.0 / 3.0) * a2yy;
+    const C o24 = C(1.0 / 3.0) * a1y - C(0.5) * a3xxy;
+    o[1] = c13 + o13;
+    o[3] = c13 - o13;
+    o[2] = c24 + o24;
+    o[4] = c24 - o24;
+    const C cd = C(1.0 / 36.0) * drho + C(1.0 / 12.0) * t;
+    const C q = C(0.25) * a2xy;
+    const C c57 = cd + q, c68 = cd - q;
+    const C o57 = C(1.0 / 12.0) * (a1x + a1y) + C(0.25) * (a3xxy + a3xyy);
+    const C o68 = C(1.0 / 12.0) * (a1y - a1x) + C(0.25) * (a3xxy - a3xyy);
+    o[5] = c57 + o57;
+    o[7] = c57 - o57;
+    o[6] = c68 + o68;
+    o[8] = c68 - o68;
+    phx = ruxx * ux;
+    phy = ruyy * uy;
 }
 
 // Moments of one node from shifted populations (eq11).
@@ -253,11 +264,11 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
         dpx = C(0.5) * (pxp - pxm);
         dpy = C(0.5) * (pyp - pym);
     }
-    C o[9], rho, ux, uy;
-    collide<C>(d, dpx, dpy, a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, o, rho, ux, uy);
+    C o[9], phx, phy;
+    collide<C>(d, dpx, dpy, a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
     if (GMODE == G_LAGGED) {
-        a.phi_out[own] = rho * ux * ux * ux;
-        a.phi_out[a.plane + own] = rho * uy * uy * uy;
+        a.phi_out[own] = phx;
+        a.phi_out[a.plane + own] = phy;
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {

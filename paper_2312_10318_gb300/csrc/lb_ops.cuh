@@ -12,8 +12,10 @@ constexpr int DIAG_THREADS = 256;
 // Kernel flavours of a lattice's step.
 enum : int { FLAV_GENERAL = 0, FLAV_PERIODIC = 1, FLAV_VECTOR = 2 };
 
-// Nodes per thread of the vectorised kernel (16 bytes of storage).
-inline int vec_width(int storage_bytes) { return 16 / storage_bytes; }
+// Nodes per thread of the vectorised kernel: 16 bytes of FP64 / FP32
+// storage, VEC16_NODES elements of 16-bit storage.
+constexpr int VEC16_NODES = 4;
+inline int vec_width(int storage_bytes) { return storage_bytes == 2 ? VEC16_NODES : 16 / storage_bytes; }
 
 // Format-independent description of a lattice's device state.
 struct State {

@@ -1,8 +1,8 @@
 // 128-bit vectorised AA step for periodic lattices without a mask.
 //
-// Each thread owns V = 16 / sizeof(S) consecutive nodes of one row (FP64 2,
-// FP32 4, FP16/BF16 8) and moves every population with one aligned 16-byte
-// load and one aligned 16-byte store.  A warp owns 32 V consecutive nodes of
+// Each thread owns V consecutive nodes of one row (FP64 2, FP32 4: 16 bytes;
+// FP16/BF16 4: 8 bytes) and moves every population with one aligned vector
+// load and one aligned vector store.  A warp owns 32 V consecutive nodes of
 // a row.  Even steps touch only the nodes' own slots.  On odd steps the slots
 // of the x-neighbours are shifted by one element: a thread loads the aligned
 // vector at its own x0 and takes the missing element from the neighbouring
@@ -14,17 +14,26 @@
 // Requires nx % V == 0 and pitch % V == 0.
 #pragma once
 #include "lb_device.cuh"
+#include "lb_ops.cuh"
 
 namespace trt {
 
 // ---- packed vectors -----------------------------------------------------------
-// P: the 16-byte register pack; get/set one element as the compute type C;
+// P: the register pack of V elements;
 // shift_up(A, w) = [w.last, A[0], ..., A[V-2]] where w is the lane-neighbour's
 // last word; shift_down(A, w) = [A[1], ..., A[V-1], w.first].
 template <typename S> struct Pk;
 
 template <> struct Pk<float> {
     using P = float4;
+    // elements 2k and 2k + 1 as compute values, and back
+    static __device__ __forceinline__ void unpack2(const P& p, int k, float& a, float& b) {
+        a = k == 0 ? p.x : p.z;
+        b = k == 0 ? p.y : p.w;
+    }
+    static __device__ __forceinline__ void pack2(P& p, int k, float a, float b) {
+        if (k == 0) { p.x = a; p.y = b; } else { p.z = a; p.w = b; }
+    }
     using W = float;  // one shuffle word
     static constexpr int V = 4;
     static __device__ __forceinline__ float get(const P& p, int v) {
@@ -43,6 +52,14 @@ template <> struct Pk<float> {
 
 template <> struct Pk<double> {
     using P = double2;
+    static __device__ __forceinline__ void unpack2(const P& p, int, double& a, double& b) {
+        a = p.x;
+        b = p.y;
+    }
+    static __device__ __forceinline__ void pack2(P& p, int, double a, double b) {
+        p.x = a;
+        p.y = b;
+    }
     using W = double;
     static constexpr int V = 2;
     static __device__ __forceinline__ double get(const P& p, int v) { return v == 0 ? p.x : p.y; }
@@ -59,32 +76,66 @@ template <> struct Pk<double> {
 
 // 8 x 16-bit elements in four 32-bit words; element 2k is the low half of
 // word k, element 2k + 1 the high half.
-template <typename H> struct Pk16 {
+template <typename H> struct Cvt2;
+template <> struct Cvt2<__half> {
+    static __device__ __forceinline__ float2 to_float2(unsigned int w) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    }
+    static __device__ __forceinline__ unsigned int from_floats(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const unsigned int*>(&h);
+    }
+};
+template <> struct Cvt2<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 to_float2(unsigned int w) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
+    static __device__ __forceinline__ unsigned int from_floats(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const unsigned int*>(&h);
+    }
+};
+
+template <int NW> struct Words;
+template <> struct Words<2> {
+    using P = uint2;
+    static __device__ __forceinline__ unsigned int get(const P& p, int k) { return k == 0 ? p.x : p.y; }
+    static __device__ __forceinline__ void set(P& p, int k, unsigned int w) {
+        if (k == 0) p.x = w; else p.y = w;
+    }
+};
+template <> struct Words<4> {
     using P = uint4;
-    using W = unsigned int;
-    static constexpr int V = 8;
-    static __device__ __forceinline__ unsigned int word(const P& p, int k) {
+    static __device__ __forceinline__ unsigned int get(const P& p, int k) {
         return k == 0 ? p.x : (k == 1 ? p.y : (k == 2 ? p.z : p.w));
     }
-    static __device__ __forceinline__ void set_word(P& p, int k, unsigned int w) {
+    static __device__ __forceinline__ void set(P& p, int k, unsigned int w) {
         if (k == 0) p.x = w; else if (k == 1) p.y = w; else if (k == 2) p.z = w; else p.w = w;
+    }
+};
+
+// 2 NW x 16-bit elements in NW 32-bit words (element 2k: low half of word k).
+template <typename H, int NW> struct Pk16 {
+    using WD = Words<NW>;
+    using P = typename WD::P;
+    using W = unsigned int;
+    static constexpr int V = 2 * NW;
+    static __device__ __forceinline__ unsigned int word(const P& p, int k) { return WD::get(p, k); }
+    static __device__ __forceinline__ void set_word(P& p, int k, unsigned int w) { WD::set(p, k, w); }
+    static __device__ __forceinline__ void unpack2(const P& p, int k, float& a, float& b) {
+        const float2 f = Cvt2<H>::to_float2(word(p, k));
+        a = f.x;
+        b = f.y;
+    }
+    static __device__ __forceinline__ void pack2(P& p, int k, float a, float b) {
+        set_word(p, k, Cvt2<H>::from_floats(a, b));
     }
     static __device__ __forceinline__ unsigned short bits(const P& p, int v) {
         const unsigned int w = word(p, v >> 1);
         return (unsigned short)((v & 1) ? (w >> 16) : (w & 0xffffu));
     }
-    static __device__ __forceinline__ float get(const P& p, int v) {
-        const unsigned short b = bits(p, v);
-        return Fmt<H>::ld(*reinterpret_cast<const H*>(&b));
-    }
-    static __device__ __forceinline__ void set(P& p, int v, float c) {
-        const H h = Fmt<H>::st(c);
-        const unsigned int b = *reinterpret_cast<const unsigned short*>(&h);
-        const unsigned int w = word(p, v >> 1);
-        set_word(p, v >> 1, (v & 1) ? ((w & 0xffffu) | (b << 16)) : ((w & 0xffff0000u) | b));
-    }
-    static __device__ __forceinline__ W last_word(const P& p) { return p.w; }
-    static __device__ __forceinline__ W first_word(const P& p) { return p.x; }
+    static __device__ __forceinline__ W last_word(const P& p) { return word(p, NW - 1); }
+    static __device__ __forceinline__ W first_word(const P& p) { return word(p, 0); }
     // an edge element loaded from memory, placed where shift_up / shift_down
     // expect it (high half for prev, low half for next: both are filled)
     static __device__ __forceinline__ W word_of(H s) {
@@ -93,18 +144,16 @@ template <typename H> struct Pk16 {
     }
     static __device__ __forceinline__ P shift_up(const P& a, W prev) {
         P r;
-        r.x = __byte_perm(prev, a.x, 0x5432);
-        r.y = __byte_perm(a.x, a.y, 0x5432);
-        r.z = __byte_perm(a.y, a.z, 0x5432);
-        r.w = __byte_perm(a.z, a.w, 0x5432);
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            set_word(r, k, __byte_perm(k == 0 ? prev : word(a, k - 1), word(a, k), 0x5432));
         return r;
     }
     static __device__ __forceinline__ P shift_down(const P& a, W next) {
         P r;
-        r.x = __byte_perm(a.x, a.y, 0x5432);
-        r.y = __byte_perm(a.y, a.z, 0x5432);
-        r.z = __byte_perm(a.z, a.w, 0x5432);
-        r.w = __byte_perm(a.w, next, 0x5432);
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            set_word(r, k, __byte_perm(word(a, k), k == NW - 1 ? next : word(a, k + 1), 0x5432));
         return r;
     }
     static __device__ __forceinline__ H elem(const P& p, int v) {
@@ -112,9 +161,13 @@ template <typename H> struct Pk16 {
         return *reinterpret_cast<const H*>(&b);
     }
 };
-template <> struct Pk<__half> : Pk16<__half> {};
-template <> struct Pk<__nv_bfloat16> : Pk16<__nv_bfloat16> {};
+// 16-bit formats run VEC16_NODES nodes per thread (8-byte vectors): measured
+// faster than 16-byte vectors, whose register footprint halves the resident
+// warps of this latency-sensitive kernel.
+template <> struct Pk<__half> : Pk16<__half, VEC16_NODES / 2> {};
+template <> struct Pk<__nv_bfloat16> : Pk16<__nv_bfloat16, VEC16_NODES / 2> {};
 
+// aligned vector load / store of one pack (16 or 8 bytes)
 template <typename S>
 __device__ __forceinline__ typename Pk<S>::P ld16(const S* p) {
     return *reinterpret_cast<const typename Pk<S>::P*>(p);
@@ -155,32 +208,7 @@ __device__ __forceinline__ void seg_step(const Args<typename Fmt<S>::C>& a, int 
     const bool edge_r = lane == 31 || x0 + V == a.nx;   // no active right lane in this segment
     const long long rowy = (long long)y * a.pitch;
 
-    // ---- gather the nine populations --------------------------------------
-    P d[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (!ODD) {
-            d[i] = active ? ld16<S>(F + (long long)i * a.plane + rowy + x0) : P{};
-        } else {
-            const int dx = ex(i), dy = ey(i);
-            const int r = dy > 0 ? ym : (dy < 0 ? yp : y);     // row of x - e_i
-            const long long base = (long long)opp(i) * a.plane + (long long)r * a.pitch;
-            const P A = active ? ld16<S>(F + base + x0) : P{};
-            if (dx == 0) {
-                d[i] = A;
-            } else if (dx > 0) {   // source x - 1
-                typename K::W w = shfl_up1(K::last_word(A));
-                if (edge_l && active) w = K::word_of(F[base + xl]);
-                d[i] = K::shift_up(A, w);
-            } else {               // source x + 1
-                typename K::W w = shfl_down1(K::first_word(A));
-                if (edge_r && active) w = K::word_of(F[base + xr]);
-                d[i] = K::shift_down(A, w);
-            }
-        }
-    }
-
-    // ---- lagged Phi: d_x Phi_xxx and d_y Phi_yyy -----------------------------
+    // ---- lagged Phi: d_x Phi_xxx and d_y Phi_yyy (first: fewer live registers)
     C dpx[V], dpy[V];
     if (GMODE == G_LAGGED) {
         const C* Px = a.phi_in + rowy;
@@ -209,19 +237,45 @@ __device__ __forceinline__ void seg_step(const Args<typename Fmt<S>::C>& a, int 
         for (int v = 0; v < V; ++v) dpx[v] = dpy[v] = C(0);
     }
 
-    // ---- collide every node of the vector ------------------------------------
+    // ---- gather the nine populations --------------------------------------
+    P d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (!ODD) {
+            d[i] = active ? ld16<S>(F + (long long)i * a.plane + rowy + x0) : P{};
+        } else {
+            const int dx = ex(i), dy = ey(i);
+            const int r = dy > 0 ? ym : (dy < 0 ? yp : y);     // row of x - e_i
+            const long long base = (long long)opp(i) * a.plane + (long long)r * a.pitch;
+            const P A = active ? ld16<S>(F + base + x0) : P{};
+            if (dx == 0) {
+                d[i] = A;
+            } else if (dx > 0) {   // source x - 1
+                typename K::W w = shfl_up1(K::last_word(A));
+                if (edge_l && active) w = K::word_of(F[base + xl]);
+                d[i] = K::shift_up(A, w);
+            } else {               // source x + 1
+                typename K::W w = shfl_down1(K::first_word(A));
+                if (edge_r && active) w = K::word_of(F[base + xr]);
+                d[i] = K::shift_down(A, w);
+            }
+        }
+    }
+
+    // ---- collide every node of the vector, two at a time ----------------------
     P o[9];
     C phx[V], phy[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        C dn[9], on[9], rho, ux, uy;
+    for (int k = 0; k < V / 2; ++k) {
+        C lo[9], hi[9], olo[9], ohi[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dn[i] = (C)K::get(d[i], v);
-        collide<C>(dn, dpx[v], dpy[v], a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, on, rho, ux, uy);
+        for (int i = 0; i < 9; ++i) K::unpack2(d[i], k, lo[i], hi[i]);
+        collide<C>(lo, dpx[2 * k], dpy[2 * k], a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, olo,
+                   phx[2 * k], phy[2 * k]);
+        collide<C>(hi, dpx[2 * k + 1], dpy[2 * k + 1], a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, ohi,
+                   phx[2 * k + 1], phy[2 * k + 1]);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) K::set(o[i], v, on[i]);
-        phx[v] = rho * ux * ux * ux;
-        phy[v] = rho * uy * uy * uy;
+        for (int i = 0; i < 9; ++i) K::pack2(o[i], k, olo[i], ohi[i]);
     }
     if (GMODE == G_LAGGED && active) {
 #pragma unroll
@@ -272,7 +326,7 @@ __device__ __forceinline__ void seg_step(const Args<typename Fmt<S>::C>& a, int 
 // Single-lattice launch: block of 256 threads = 8 warps, warp w of block b
 // owns segment s = 8 b + w of the (row, segment) list.
 template <typename S, bool ODD, int GMODE>
-__global__ void __launch_bounds__(256) k_step_vec(Args<typename Fmt<S>::C> a, int segs_per_row) {
+__global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3) k_step_vec(Args<typename Fmt<S>::C> a, int segs_per_row) {
     constexpr int V = Pk<S>::V;
     const int lane = (int)threadIdx.x & 31;
     const long long s = (long long)blockIdx.x * 8 + ((int)threadIdx.x >> 5);

@@ -14,7 +14,7 @@ from paper_2312_10318_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-V = {"f64": 2, "f32": 4, "f16": 8, "bf16": 8}
+V = {"f64": 2, "f32": 4, "f16": 4, "bf16": 4}
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
 ULP = {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}
 TINY = {"f16": 2.0 ** -23, "bf16": 1e-30}   # FP16 subnormal spacing is 2^-24
