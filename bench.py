@@ -197,6 +197,44 @@ def cpu_baseline(problems, seconds: float = 12.0):
                       f"{dt:.1f} s"}
 
 
+def run_serving(args) -> dict:
+    """The served-stream measurement: a seeded Poisson stream of Taylor-Green,
+    double-shear-layer and channel solves (sides log-uniform 64..4096, Re
+    log-uniform 1..1e6, FP64/FP32/FP16 uniform), served by the continuous-batching
+    server with the precision guard, and by the FP64 one-lattice-at-a-time
+    reference on the same stream."""
+    from paper_2312_10318_gb300 import serve as S
+    lo, hi = (max(1, int(1000 * args.serve_scale)), max(2, int(20000 * args.serve_scale)))
+    reqs = S.make_stream(args.serve_requests, seed=0, rate=args.serve_rate, steps_range=(lo, hi))
+    work = sum(r.work for r in reqs)
+    guard = S.PrecisionGuard()
+    srv = S.Server(hbm_budget=args.serve_budget_gb * 1e9, chunk=512, guard=guard)
+    res = srv.run(reqs, realtime=True)
+    by_rid = {r.rid: r for r in reqs}
+    gsum = {}
+    for rid, storage, e_end, pred, tol in guard.checked:
+        g = gsum.setdefault(storage, {"checked": 0, "widened": 0, "predicted": []})
+        g["checked"] += 1
+        g["widened"] += int(not (pred <= tol))
+        g["predicted"].append(pred)
+    for g in gsum.values():
+        g["predicted_median"] = float(np.median(g.pop("predicted")))
+    finished = {}
+    for r in res:
+        finished[r.storage] = finished.get(r.storage, 0) + 1
+    out = {"stream": {"requests": len(reqs), "seed": 0, "rate_per_s": args.serve_rate,
+                      "steps": [lo, hi], "sides": [64, 4096], "re": [1, 1e6],
+                      "storages": ["f64", "f32", "f16"], "node_updates": work,
+                      "hbm_budget_gb": args.serve_budget_gb},
+           "batched": S.summarize(res, srv.makespan, srv.node_updates),
+           "precision_guard": {"stated_bounds": S.STATED_BOUND, "by_storage": gsum,
+                               "finished_in": finished}}
+    if not args.no_serve_reference:
+        ref = S.run_fifo(reqs, storage="f64", realtime=True)
+        out["fp64_fifo"] = S.summarize(ref, S.run_fifo.makespan, work)
+    return out
+
+
 def run_reference(args, problems, desc, budget_s: float = 60.0):
     """The FP64 CPU oracle on the workload, on the host cores (rank 0 only).  Each
     step advances every lattice of the workload by one time step on a strip of
@@ -263,6 +301,13 @@ def main():
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "vector"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
+    ap.add_argument("--no-serve-reference", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-rate", type=float, default=16.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-scale", type=float, default=0.05,
+                    help="step counts of the stream: [1000, 20000] x scale")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--mode", default="batch", choices=["batch", "single"],
                     help="batch: one launch per time step for all lattices; single: one per lattice")
     args = ap.parse_args()
@@ -415,6 +460,8 @@ def main():
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(problems)
+        if not args.no_serve:
+            line["serving"] = run_serving(args)
         print(json.dumps(line), flush=True)
     batch.close()
     for lat in lats:

@@ -70,7 +70,8 @@ template <typename C> struct Args {
     int nx, ny, pitch;
     long long plane;      // ny * pitch
     int px, py;           // periodic flags
-    C k1, k2, kf;         // 1 - 1/tau1, 1 - 1/tau2, 1 - 1/(2 tau1)
+    C k1, k1lo, k2, k2lo; // 1 - 1/tau as a hi + lo pair (lo = 0 for FP64)
+    C kf;                 // 1 - 1/(2 tau1)
     C gx, gy, rho0;
     C corr[9];            // moving-wall term 2 w_i rho_w (e_i.u_w) / c_s^2
 };
@@ -147,7 +148,7 @@ __device__ __forceinline__ long long pop_loc(long long plane, const long long (&
 // of eq2.  In D2Q9 every Hermite contraction collapses: with
 //   a1 = j + F,
 //   a2_ab = rho u_a u_b + (1 - 1/tau1) A_ab + (1 - 1/(2 tau1))(F_a u_b + u_a F_b)
-//           - (1 - 1/(2 tau1)) d_g Phi_abg,
+//           - (1 - 1/(2 tau1)) d_g Phi_abg   (rho u_a u_b + A_ab = sum H_ab f),
 //   a3_xxy = rho u_x^2 u_y + (1 - 1/tau2) A_xxy  (and xyy alike),
 // f*_i = w_i [rho + 3 e_i.a1 + 9/2 H_i,ab a2_ab + 27/2 (H_i,xxy a3_xxy +
 // H_i,xyy a3_xyy)], because 1/(2 c_s^4) = 1/(6 c_s^6) = 9/2, H_xxx = H_yyy = 0
@@ -156,9 +157,9 @@ __device__ __forceinline__ long long pop_loc(long long plane, const long long (&
 // their partial sums (the compiler may not reassociate float additions).
 // Returns Phi_xxx = rho u_x^3 and Phi_yyy = rho u_y^3 of the node (eq11 u).
 template <typename C>
-__device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k2,
-                                        const C kf, const C gx, const C gy, const C rho0,
-                                        C (&o)[9], C& phx, C& phy) {
+__device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k1lo,
+                                        const C k2, const C k2lo, const C kf, const C gx,
+                                        const C gy, const C rho0, C (&o)[9], C& phx, C& phy) {
     const C third = C(1) / C(3);
     // raw moments of the shifted populations
     const C s13 = d[1] + d[3], m13 = d[1] - d[3];
@@ -181,19 +182,34 @@ __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k
     const C rux = rho * ux, ruy = rho * uy;
     const C ruxx = rux * ux, ruyy = ruy * uy, ruxy = rux * uy;
     const C rxxy = ruxx * uy, rxyy = ruyy * ux;
-    // eq9 with the equilibrium moments of eq9_2 (A_x = -F_x/2 is folded into a1)
+    // Hermite moments sum H f: second order (H_xx = e_x^2 - 1/3, ...) and the
+    // surviving third-order components; minus the equilibrium moments of
+    // eq9_2 they are the non-equilibrium projections A of eq9 (A_x = -F_x/2
+    // is folded into a1)
     const C drho3 = third * drho;
-    const C Axx = (s13 + sd) - drho3 - ruxx;
-    const C Ayy = (s24 + sd) - drho3 - ruyy;
-    const C Axy = pxy - ruxy;
-    const C Axxy = qxxy - third * jy - rxxy;
-    const C Axyy = qxyy - third * jx - rxyy;
+    const C Pxx = (s13 + sd) - drho3, Pyy = (s24 + sd) - drho3;
+    const C Qxxy = qxxy - third * jy, Qxyy = qxyy - third * jx;
+    const C Axx = Pxx - ruxx, Ayy = Pyy - ruyy, Axy = pxy - ruxy;
+    const C Axxy = Qxxy - rxxy, Axyy = Qxyy - rxyy;
+    // relaxation: (1 - 1/tau) A with 1 - 1/tau carried as hi + lo, so the rate
+    // 1/tau stays exact to ~2^-48 even when tau is large (FP32 alone would
+    // round 1 - 1/tau to 2^-24 absolute, i.e. 1/tau to 2^-24 tau relative)
+    // (FP64 needs no low part: its rounding of 1 - 1/tau is below 1e-11 of the
+    // rate for any tau this library accepts in practice)
+    constexpr bool split = sizeof(C) < 8;
     const C a1x = jx + Fx, a1y = jy + Fy;
-    const C a2xx = ruxx + k1 * Axx + kf * (C(2) * Fx * ux - dpx);
-    const C a2yy = ruyy + k1 * Ayy + kf * (C(2) * Fy * uy - dpy);
-    const C a2xy = ruxy + k1 * Axy + kf * (Fx * uy + ux * Fy);
-    const C a3xxy = rxxy + k2 * Axxy;
-    const C a3xyy = rxyy + k2 * Axyy;
+    C r2xx = ruxx + k1 * Axx, r2yy = ruyy + k1 * Ayy, r2xy = ruxy + k1 * Axy;
+    C a3xxy = rxxy + k2 * Axxy, a3xyy = rxyy + k2 * Axyy;
+    if (split) {
+        r2xx += k1lo * Axx;
+        r2yy += k1lo * Ayy;
+        r2xy += k1lo * Axy;
+        a3xxy += k2lo * Axxy;
+        a3xyy += k2lo * Axyy;
+    }
+    const C a2xx = r2xx + kf * (C(2) * Fx * ux - dpx);
+    const C a2yy = r2yy + kf * (C(2) * Fy * uy - dpy);
+    const C a2xy = r2xy + kf * (Fx * uy + ux * Fy);
     // reconstruction, w_i folded in: w0 = 4/9, w1..4 = 1/9, w5..8 = 1/36
     const C t = a2xx + a2yy;
     o[0] = C(4.0 / 9.0) * drho - C(2.0 / 3.0) * t;
@@ -265,7 +281,7 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
         dpy = C(0.5) * (pyp - pym);
     }
     C o[9], phx, phy;
-    collide<C>(d, dpx, dpy, a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
+    collide<C>(d, dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
     if (GMODE == G_LAGGED) {
         a.phi_out[own] = phx;
         a.phi_out[a.plane + own] = phy;

@@ -16,8 +16,11 @@ static Args<C> make_args(const State& s, bool swap_phi = false) {
     a.mask = s.mask;
     a.nx = s.nx; a.ny = s.ny; a.pitch = s.pitch; a.plane = s.plane;
     a.px = s.px; a.py = s.py;
-    a.k1 = (C)(1.0 - 1.0 / s.tau1);
-    a.k2 = (C)(1.0 - 1.0 / s.tau2);
+    const double k1 = 1.0 - 1.0 / s.tau1, k2 = 1.0 - 1.0 / s.tau2;
+    a.k1 = (C)k1;
+    a.k1lo = (C)(k1 - (double)a.k1);   // 0 when C is double
+    a.k2 = (C)k2;
+    a.k2lo = (C)(k2 - (double)a.k2);
     a.kf = (C)(1.0 - 1.0 / (2.0 * s.tau1));
     a.gx = (C)s.gx; a.gy = (C)s.gy; a.rho0 = (C)s.rho0;
     for (int i = 0; i < 9; ++i) {

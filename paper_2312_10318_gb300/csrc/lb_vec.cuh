@@ -270,9 +270,9 @@ __device__ __forceinline__ void seg_step(const Args<typename Fmt<S>::C>& a, int 
         C lo[9], hi[9], olo[9], ohi[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) K::unpack2(d[i], k, lo[i], hi[i]);
-        collide<C>(lo, dpx[2 * k], dpy[2 * k], a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, olo,
+        collide<C>(lo, dpx[2 * k], dpy[2 * k], a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, olo,
                    phx[2 * k], phy[2 * k]);
-        collide<C>(hi, dpx[2 * k + 1], dpy[2 * k + 1], a.k1, a.k2, a.kf, a.gx, a.gy, a.rho0, ohi,
+        collide<C>(hi, dpx[2 * k + 1], dpy[2 * k + 1], a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, ohi,
                    phx[2 * k + 1], phy[2 * k + 1]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) K::pack2(o[i], k, olo[i], ohi[i]);

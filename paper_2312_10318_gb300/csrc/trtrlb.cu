@@ -74,6 +74,16 @@ void release(trtrlb_lattice* h) {
     delete h;
 }
 
+// Staging buffer for host transfers (11 n doubles), allocated on first use.
+cudaError_t ensure_stage(trtrlb_lattice* h) {
+    if (h->stage) return cudaSuccess;
+    const size_t bytes = sizeof(double) * 11 * (size_t)h->p.nx * h->p.ny;
+    const cudaError_t e = cudaMalloc((void**)&h->stage, bytes);
+    if (e == cudaSuccess) h->bytes += (int64_t)bytes;
+    else h->stage = nullptr;
+    return e;
+}
+
 // Resolves tau_s2 from tau_s2 / magic (eq_a29).  Returns 0 or an error code.
 int resolve_tau2(const trtrlb_params& p, double* tau2, char* err) {
     const bool has_t2 = !std::isnan(p.tau_s2), has_m = !std::isnan(p.magic);
@@ -174,7 +184,6 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         return e == cudaSuccess;
     };
     bool ok = alloc(&h->f, es * 9 * plane) && alloc(&h->phi, ps * 4 * plane) &&
-              alloc((void**)&h->stage, sizeof(double) * 11 * n) &&
               alloc((void**)&h->dout, sizeof(double) * 8);
     if (ok && mask) ok = alloc((void**)&h->mask, (size_t)plane);
     if (ok && !ghosts.empty()) ok = alloc((void**)&h->ghosts, sizeof(int) * ghosts.size());
@@ -258,6 +267,8 @@ int trtrlb_init(trtrlb_t h, const double* rho, const double* ux, const double* u
         if (on_device(src[q])) {
             dev[q] = src[q];
         } else {
+            e = ensure_stage(h);
+            if (e != cudaSuccess) break;
             e = cudaMemcpyAsync(h->stage + q * n, src[q], nb, cudaMemcpyHostToDevice, h->stream);
             dev[q] = h->stage + q * n;
         }
@@ -287,10 +298,15 @@ int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy) {
     double* dst[3] = {rho, ux, uy};
     double* dev[3] = {nullptr, nullptr, nullptr};
     bool host = false;
+    for (int q = 0; q < 3; ++q)
+        if (dst[q] && !on_device(dst[q])) host = true;
+    if (host) {
+        const cudaError_t se = ensure_stage(h);
+        if (se != cudaSuccess) return cuda_fail(h->err, se, "moments staging");
+    }
     for (int q = 0; q < 3; ++q) {
         if (!dst[q]) continue;
-        if (on_device(dst[q])) dev[q] = dst[q];
-        else { dev[q] = h->stage + q * n; host = true; }
+        dev[q] = on_device(dst[q]) ? dst[q] : h->stage + q * n;
     }
     cudaError_t e = TRT_DISPATCH(h->p.storage, moments(h->s, dev[0], dev[1], dev[2], h->stream));
     for (int q = 0; q < 3 && e == cudaSuccess; ++q)
@@ -305,6 +321,10 @@ int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
     if (!h) return TRTRLB_EINVAL;
     h->err[0] = 0;
     const size_t n = (size_t)h->p.nx * h->p.ny;
+    if ((f && !on_device(f)) || (phi && !on_device(phi))) {
+        const cudaError_t se = ensure_stage(h);
+        if (se != cudaSuccess) return cuda_fail(h->err, se, "get_f staging");
+    }
     double* df = f && !on_device(f) ? h->stage : f;
     double* dp = phi && !on_device(phi) ? h->stage + 9 * n : phi;
     cudaError_t e = TRT_DISPATCH(h->p.storage, get_f(h->s, df, dp, h->stream));
@@ -330,7 +350,8 @@ int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi) {
     const double* df = f;
     const double* dp = phi;
     cudaError_t e = cudaSuccess;
-    if (!on_device(f)) {
+    if (!on_device(f) || (phi && !on_device(phi))) e = ensure_stage(h);
+    if (e == cudaSuccess && !on_device(f)) {
         e = cudaMemcpyAsync(h->stage, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         df = h->stage;
     }

@@ -91,6 +91,7 @@ class Lattice:
         h = C.c_void_p()
         _lib.check(lib.trtrlb_create(C.byref(p), None if m is None else m.ctypes.data,
                                      C.c_void_p(stream), C.byref(h)))
+        self._stream = stream
         self._h = h
         self._lib = lib
         self.params = p
@@ -135,6 +136,7 @@ class Lattice:
     def set_stream(self, stream):
         s = stream if isinstance(stream, int) else stream.cuda_stream
         self._chk(self._lib.trtrlb_set_stream(self._h, C.c_void_p(s)))
+        self._stream = s
 
     def set_kernel(self, variant="auto", tile_w=0):
         """Kernel shape: 'auto' | 'scalar' | 'vector', scalar tile width (0 keeps it)."""

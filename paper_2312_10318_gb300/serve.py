@@ -1,0 +1,448 @@
+"""Continuous-batching service for lattice solves.
+
+Requests (a Taylor-Green vortex, a double shear layer or a force-driven
+channel of some size, Reynolds number, step count and storage format) arrive
+over time.  The server keeps every admitted lattice resident in HBM, admits
+waiting requests whenever the HBM budget allows, and advances all admitted
+lattices together: one batched kernel launch per storage format and time step
+(`Batch`, replayed from CUDA graphs), in chunks that end exactly when the next
+request completes.  A finished lattice is retired at the chunk boundary: its
+FP64 diagnostics are the result, its memory goes back to the budget, and
+requests that arrived meanwhile are admitted before the next chunk.
+
+Time-to-solution is measured from arrival to retirement.  `run_fifo` is the
+plain reference: FP64 storage, one request at a time, one kernel launch per
+time step.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import params as P
+from . import workloads as W
+
+KINDS = ("taylor_green", "double_shear_layer", "poiseuille")
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str
+    n: int
+    re: float
+    steps: int
+    storage: str
+    arrival: float = 0.0      # seconds after the stream starts
+
+    @property
+    def work(self) -> int:
+        """Node updates of the solve."""
+        return self.n * self.n * self.steps
+
+
+@dataclass
+class Result:
+    rid: int
+    status: str               # "ok" | "unstable" | "rejected"
+    storage: str              # storage the solve finished in
+    steps: int
+    diagnostics: dict
+    t_arrival: float
+    t_admit: float
+    t_finish: float
+    fallback: bool = False
+
+    @property
+    def latency(self) -> float:
+        return self.t_finish - self.t_arrival
+
+
+def lattice_bytes(n_x: int, n_y: int, storage: str) -> int:
+    """Device bytes of one lattice as the library allocates it: populations
+    (9 per node), two Phi buffers of two components, the diagnostics scratch."""
+    pitch = (n_x + 63) // 64 * 64
+    plane = pitch * n_y
+    phi = 8 if storage == "f64" else 4
+    blocks = max(1, min(1216, -(-n_x * n_y // 256)))
+    return 9 * STORAGE_BYTES[storage] * plane + 4 * phi * plane + 8 * 8 * blocks + 64
+
+
+def make_stream(n_requests: int, seed: int = 0, rate: float = 1.0, n_min: int = 64,
+                n_max: int = 4096, re_range=(1.0, 1e6), steps_range=(1000, 20000),
+                storages=("f64", "f32", "f16"), kinds=KINDS) -> list:
+    """Seeded request stream: Poisson arrivals at `rate` per second, kind and
+    storage uniform, side log-uniform in [n_min, n_max] rounded to a multiple of
+    8, Re log-uniform in re_range, steps uniform in steps_range."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n_requests):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) / 8.0)) * 8
+        n = max(8, n)
+        re = math.exp(rng.uniform(math.log(re_range[0]), math.log(re_range[1])))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        out.append(Request(rid, str(rng.choice(kinds)), n, re, steps, str(rng.choice(storages)), t))
+    return out
+
+
+def problem_of(req: Request) -> W.Problem:
+    """The lattice problem of a request (fields built on the host)."""
+    if req.kind == "taylor_green":
+        return W.taylor_green(req.n, u0=0.04, re=req.re, tau_s2=0.625, steps=req.steps)
+    if req.kind == "double_shear_layer":
+        return W.double_shear_layer(req.n, re=req.re, steps=req.steps)
+    if req.kind == "poiseuille":
+        tau = P.tau_from_reynolds(req.re, 0.01, req.n)
+        return W.poiseuille(req.n, tau, 3.0 / 16.0, nx=req.n, u_c=0.01, steps=req.steps)
+    raise ValueError(req.kind)
+
+
+@dataclass
+class Spec:
+    """Lattice parameters of a request (no fields)."""
+    nx: int
+    ny: int
+    tau_s: float
+    tau_s2: float
+    periodic: tuple
+    g: tuple
+    meta: dict
+
+    def lattice_kwargs(self) -> dict:
+        return dict(tau_s2=self.tau_s2, periodic=self.periodic, g=self.g)
+
+
+def spec_of(req: Request) -> Spec:
+    """The parameters problem_of(req) would give, without building fields."""
+    n = req.n
+    if req.kind == "taylor_green":
+        tau = P.tau_from_reynolds(req.re, 0.04, n)
+        return Spec(n, n, tau, 0.625, (True, True), (0.0, 0.0),
+                    dict(u0=0.04, k=2.0 * math.pi / n))
+    if req.kind == "double_shear_layer":
+        tau = P.tau_from_reynolds(req.re, 0.04, n)
+        return Spec(n, n, tau, 0.625, (True, True), (0.0, 0.0),
+                    dict(u_c=0.04, kappa=80.0, delta=0.05))
+    if req.kind == "poiseuille":
+        tau = P.tau_from_reynolds(req.re, 0.01, n)
+        g = P.poiseuille_acceleration(0.01, P.nu_from_tau(tau), n)
+        return Spec(n, n, tau, P.tau2_from_magic(tau, 3.0 / 16.0), (True, False), (g, 0.0),
+                    dict(u_c=0.01))
+    raise ValueError(req.kind)
+
+
+def device_fields(req: Request, pr, device="cuda"):
+    """(ux, uy, rho) of the request's initial state as CUDA float64 tensors,
+    built on the device with the same formulas as workloads.py (so a 4096^2
+    request does not stall the host)."""
+    import torch
+    n = req.n
+    if req.kind == "poiseuille":
+        z = torch.zeros((n, n), dtype=torch.float64, device=device)
+        return z, z.clone(), None
+    x = torch.arange(n, dtype=torch.float64, device=device)
+    Y, X = torch.meshgrid(x, x, indexing="ij")
+    if req.kind == "taylor_green":
+        u0, k = pr.meta["u0"], pr.meta["k"]
+        ux = -u0 * torch.cos(k * X) * torch.sin(k * Y)
+        uy = u0 * torch.sin(k * X) * torch.cos(k * Y)
+        rho = 1.0 - u0 * u0 * 0.75 * (torch.cos(2 * k * X) + torch.cos(2 * k * Y))
+        return ux.contiguous(), uy.contiguous(), rho.contiguous()
+    uc, kappa, delta = pr.meta["u_c"], pr.meta["kappa"], pr.meta["delta"]
+    Xs, Ys = X / n, Y / n
+    ux = torch.where(Ys <= 0.5, uc * torch.tanh(kappa * (Ys - 0.25)), uc * torch.tanh(kappa * (0.75 - Ys)))
+    uy = uc * delta * torch.sin(2.0 * math.pi * (Xs + 0.25))
+    return ux.contiguous(), uy.contiguous(), None
+
+
+# Stated end-of-run velocity error (relative L2 of u against FP64 storage,
+# eq_n1) per storage format: measured on the Taylor-Green vortex (64^2, u0 =
+# 0.04, Re = 100, 1000 steps: FP32 1.0e-5, FP16 6.1e-3, BF16 8.1e-2) with margin.
+STATED_BOUND = {"f64": 0.0, "f32": 1e-4, "f16": 1e-2, "bf16": 1e-1}
+
+
+def l2(a, b) -> float:
+    """Relative L2 error of eq_n1."""
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    den = float((b * b).sum())
+    return math.sqrt(float(((a - b) ** 2).sum()) / den) if den > 0 else float(np.abs(a - b).max())
+
+
+ORDER = ("f16", "bf16", "f32", "f64")
+WIDER = {"bf16": "f32", "f16": "f32", "f32": "f64"}
+
+
+def velocity_scale(spec) -> float:
+    """Characteristic speed of a request (u0 or u_c of its problem)."""
+    m = spec.meta
+    return float(m.get("u0", m.get("u_c", 0.04)))
+
+
+class PrecisionGuard:
+    """Admission-time check of a reduced-precision solve against FP64.
+
+    The lattice and an FP64 shadow start from the same fields and advance a
+    short probe (at most `probe` steps, a sixteenth of the run).  The velocity
+    error against the shadow, RMS(u - u_FP64) / U with U the request's
+    characteristic speed, is taken at half the probe and at its end and fitted
+    as e(t) = e0 + r t (e0: the one-time rounding of the initial state into the
+    format; r: its growth per step); the end-of-run error is predicted as
+    e0 + r x steps.  If the prediction exceeds the tolerance (default: the
+    format's stated bound, else `tol`) the solve moves to the next wider format
+    (FP16/BF16 -> FP32 -> FP64), which is checked the same way; FP64 needs no
+    check.  The kept lattice restarts at t = 0.  Call it with the lattice's
+    stream current (the server does): the probe's fields live on that stream."""
+
+    def __init__(self, tol: Optional[float] = None, probe: int = 64):
+        self.tol = tol
+        self.probe = probe
+        self.checked = []      # (rid, storage, e_end, predicted, tol)
+
+    @staticmethod
+    def _err(a, b, scale: float) -> float:
+        _, ux, uy = a.moments()
+        _, vx, vy = b.moments()
+        d2 = ((ux - vx) ** 2 + (uy - vy) ** 2).mean()
+        return math.sqrt(float(d2)) / scale
+
+    def _predict(self, req, lat, shadow, scale, m) -> float:
+        lat.step(m // 2)
+        shadow.step(m // 2)
+        e_half = self._err(lat, shadow, scale)
+        lat.step(m - m // 2)
+        shadow.step(m - m // 2)
+        e_end = self._err(lat, shadow, scale)
+        rate = max(0.0, (e_end - e_half) / (m - m // 2))
+        pred = e_end + rate * (req.steps - m)
+        return e_end, pred
+
+    def __call__(self, req: Request, lat):
+        from .lattice import Lattice
+        if req.storage == "f64":
+            return lat
+        m = max(2, min(self.probe, req.steps // 16)) // 2 * 2
+        sp = spec_of(req)
+        scale = velocity_scale(sp)
+        fields = device_fields(req, sp)
+        shadow = Lattice(sp.nx, sp.ny, sp.tau_s, storage="f64", stream=lat._stream, **sp.lattice_kwargs())
+        storage, cur = req.storage, lat
+        while storage != "f64":
+            tol = self.tol if self.tol is not None else STATED_BOUND[storage]
+            shadow.init(*fields)
+            e_end, pred = self._predict(req, cur, shadow, scale, m)
+            self.checked.append((req.rid, storage, e_end, pred, tol))
+            if math.isfinite(pred) and pred <= tol:
+                break
+            storage = WIDER[storage]
+            if cur is not lat:
+                cur.close()
+            if storage != "f64":
+                cur = Lattice(sp.nx, sp.ny, sp.tau_s, storage=storage, stream=lat._stream,
+                              **sp.lattice_kwargs())
+                cur.init(*fields)
+        if storage == "f64":
+            if cur is not lat and cur is not shadow:
+                cur.close()
+            shadow.init(*fields)
+            return shadow
+        shadow.close()
+        cur.init(*fields)
+        return cur
+
+
+@dataclass
+class _Active:
+    req: Request
+    lat: object
+    remaining: int
+    t_admit: float
+    nbytes: int
+    storage: str
+    fallback: bool = False
+
+
+class Server:
+    """Continuous batching of lattice solves on the current CUDA device.
+
+    hbm_budget: bytes the admitted lattices may occupy.  chunk: the most steps
+    advanced between two scheduling points.  check_every: chunks between
+    NaN/instability checks of every active lattice (0: only at retirement).
+    guard: optional callable(request, lattice) -> lattice applied on admission
+    (the precision guard may return an FP64 replacement).  max_u: |u| above
+    which a solve counts as unstable.  on_retire: optional
+    callable(request, lattice, status) run before a finished lattice is freed
+    (to fetch fields).  max_active_nodes: admission stops while the admitted
+    lattices hold this many nodes (the GPU is bandwidth-saturated well below
+    it), so requests finish closer to arrival order."""
+
+    def __init__(self, hbm_budget: float = 150e9, chunk: int = 512, check_every: int = 8,
+                 guard: Optional[Callable] = None, max_u: float = 0.5, stream=None,
+                 on_retire: Optional[Callable] = None, max_active_nodes: float = 48e6):
+        import torch
+        from .lattice import Batch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.batch = Batch(self.stream)
+        self.budget = float(hbm_budget)
+        self.chunk = int(chunk)
+        self.check_every = int(check_every)
+        self.guard = guard
+        self.max_u = max_u
+        self.on_retire = on_retire    # callable(request, lattice, status) before a lattice is freed
+        self.max_active_nodes = float(max_active_nodes)
+        self.active_nodes = 0
+        self.used = 0
+        self.node_updates = 0
+        self.log = []
+
+    def _admit(self, req: Request, now: float) -> Optional[_Active]:
+        import torch
+        from .lattice import Lattice
+        nbytes = lattice_bytes(req.n, req.n, req.storage)
+        if self.used + nbytes > self.budget:
+            return None
+        # enough nodes in flight saturate HBM; admitting more only stretches
+        # every solve (the first request is always admitted)
+        if self.active_nodes > 0 and self.active_nodes + req.n * req.n > self.max_active_nodes:
+            return None
+        pr = spec_of(req)
+        # fields and init on the server's stream: the fields' memory is then
+        # stream-ordered with the kernels that read it
+        with torch.cuda.stream(self.stream):
+            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=req.storage, stream=self.stream,
+                          **pr.lattice_kwargs())
+            ux, uy, rho = device_fields(req, pr)
+            lat.init(ux, uy, rho)
+            act = _Active(req, lat, req.steps, now, nbytes, req.storage)
+            if self.guard is not None:
+                lat2 = self.guard(req, lat)
+                if lat2 is not lat:
+                    act.fallback = True
+                    act.storage = lat2.storage
+                    act.nbytes = lattice_bytes(req.n, req.n, lat2.storage)
+                    lat.close()
+                    act.lat = lat2
+        self.used += act.nbytes
+        self.active_nodes += req.n * req.n
+        return act
+
+    def _retire(self, a: _Active, now: float, status: str, diag: dict) -> Result:
+        if self.on_retire is not None:
+            self.on_retire(a.req, a.lat, status)
+        a.lat.close()
+        self.used -= a.nbytes
+        self.active_nodes -= a.req.n * a.req.n
+        return Result(a.req.rid, status, a.storage, a.req.steps - a.remaining, diag, a.req.arrival,
+                      a.t_admit, now, a.fallback)
+
+    def _unstable(self, d: dict) -> bool:
+        return d["nonfinite"] > 0 or not math.isfinite(d["max_u"]) or d["max_u"] > self.max_u
+
+    def run(self, requests: list, realtime: bool = True) -> list:
+        """Serves the stream; with realtime=False every request is available at once."""
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        waiting, active, results = [], [], []
+        members = None
+        chunks = 0
+        t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0
+        while pending or waiting or active:
+            now = clock()
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.pop(0))
+            # admission, first come first served
+            while waiting:
+                req = waiting[0]
+                if lattice_bytes(req.n, req.n, req.storage) > self.budget:
+                    waiting.pop(0)
+                    results.append(Result(req.rid, "rejected", req.storage, 0, {}, req.arrival, now, now))
+                    continue
+                a = self._admit(req, clock())
+                if a is None:
+                    break
+                waiting.pop(0)
+                active.append(a)
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.05, pending[0].arrival - clock())))
+                continue
+            lats = [a.lat for a in active]
+            if members is None or len(members) != len(lats) or any(x is not y for x, y in zip(members, lats)):
+                self.batch.set(lats)
+                members = lats
+            n = min(self.chunk, min(a.remaining for a in active))
+            self.batch.step(n)
+            self.stream.synchronize()
+            chunks += 1
+            self.node_updates += n * sum(a.req.n * a.req.n for a in active)
+            for a in active:
+                a.remaining -= n
+            now = clock()
+            check = self.check_every > 0 and chunks % self.check_every == 0
+            keep = []
+            for a in active:
+                if a.remaining == 0 or check:
+                    d = a.lat.diagnostics()
+                    if self._unstable(d):
+                        results.append(self._retire(a, now, "unstable", d))
+                        continue
+                    if a.remaining == 0:
+                        results.append(self._retire(a, now, "ok", d))
+                        continue
+                keep.append(a)
+            if len(keep) != len(active):
+                active = keep
+                members = None
+                if not active:
+                    self.batch.set([])
+        self.makespan = clock()
+        return sorted(results, key=lambda r: r.rid)
+
+
+def run_fifo(requests: list, storage: str = "f64", realtime: bool = True) -> list:
+    """Reference service: each request alone, in arrival order, in `storage`,
+    one kernel launch per time step (no batching, no graphs)."""
+    import torch
+    from .lattice import Lattice
+    stream = torch.cuda.Stream()
+    results = []
+    t0 = time.perf_counter()
+    clock = lambda: time.perf_counter() - t0
+    for req in sorted(requests, key=lambda r: r.arrival):
+        if realtime and req.arrival > clock():
+            time.sleep(req.arrival - clock())
+        t_admit = clock()
+        pr = spec_of(req)
+        with torch.cuda.stream(stream):
+            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, stream=stream, **pr.lattice_kwargs())
+            ux, uy, rho = device_fields(req, pr)
+            lat.init(ux, uy, rho)
+        lat.step(req.steps)
+        d = lat.diagnostics()
+        status = "unstable" if d["nonfinite"] > 0 or not math.isfinite(d["max_u"]) or d["max_u"] > 0.5 else "ok"
+        lat.close()
+        results.append(Result(req.rid, status, storage, req.steps, d, req.arrival, t_admit, clock()))
+    run_fifo.makespan = clock()
+    return results
+
+
+def summarize(results: list, makespan: float, node_updates: Optional[float] = None) -> dict:
+    """solves/s, aggregate MLUPS, p50/p99 time-to-solution (s) of a served stream."""
+    done = [r for r in results if r.status in ("ok", "unstable")]
+    lat = np.array([r.latency for r in done]) if done else np.array([float("nan")])
+    if node_updates is None:
+        node_updates = 0.0
+    return {"requests": len(results), "completed": sum(r.status == "ok" for r in results),
+            "unstable": sum(r.status == "unstable" for r in results),
+            "rejected": sum(r.status == "rejected" for r in results),
+            "fallbacks": sum(r.fallback for r in results),
+            "makespan_s": makespan, "solves_per_s": len(done) / makespan if makespan > 0 else float("nan"),
+            "mlups": node_updates / makespan / 1e6 if makespan > 0 else float("nan"),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}
