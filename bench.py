@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D2Q9 TRT-RLB MLUPS & % HBM roofline; served solves/s, p50/p99 latency"
 UNIT = "MLUPS"
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
-PHI_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f64dw": 8}
+PHI_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4, "f64dw": 8}
 
 
 def workload(name: str, size=None, storage=None):
@@ -205,10 +205,28 @@ def run_serving(args) -> dict:
     reference on the same stream."""
     from paper_2312_10318_gb300 import serve as S
     lo, hi = (max(1, int(1000 * args.serve_scale)), max(2, int(20000 * args.serve_scale)))
-    reqs = S.make_stream(args.serve_requests, seed=0, rate=args.serve_rate, steps_range=(lo, hi))
+    reqs = S.make_stream(args.serve_requests, seed=0, rate=1.0, steps_range=(lo, hi))
     work = sum(r.work for r in reqs)
     guard = S.PrecisionGuard()
-    srv = S.Server(hbm_budget=args.serve_budget_gb * 1e9, chunk=512, guard=guard)
+    from paper_2312_10318_gb300.tune import Tuner
+    tuner = Tuner(persist=False, steps=32, reps=2)
+    # kernel shapes of every format a request may run in (FP64 needs none),
+    # tuned before the stream starts: a deployment-time cost, like capturing graphs
+    t0 = time.perf_counter()
+    tuner.warm(S.shapes_of(reqs, storages=("f32", "f16") + (("f64dw",) if args.serve_fp64_as == "f64dw" else ())))
+    tune_s = time.perf_counter() - t0
+    # capacity: the whole stream available at once; then arrivals at the rate
+    # that offers `serve_load` x that capacity (Poisson inter-arrival times of
+    # the seeded stream, rescaled)
+    cal = S.Server(hbm_budget=args.serve_budget_gb * 1e9, chunk=512, guard=S.PrecisionGuard(),
+                   tuner=tuner, fp64_as=args.serve_fp64_as)
+    cal.run(reqs, realtime=False)
+    capacity = len(reqs) / cal.makespan
+    rate = args.serve_rate if args.serve_rate > 0 else args.serve_load * capacity
+    for r in reqs:
+        r.arrival = r.arrival / rate
+    srv = S.Server(hbm_budget=args.serve_budget_gb * 1e9, chunk=512, guard=guard, tuner=tuner,
+                   fp64_as=args.serve_fp64_as)
     res = srv.run(reqs, realtime=True)
     by_rid = {r.rid: r for r in reqs}
     gsum = {}
@@ -222,10 +240,12 @@ def run_serving(args) -> dict:
     finished = {}
     for r in res:
         finished[r.storage] = finished.get(r.storage, 0) + 1
-    out = {"stream": {"requests": len(reqs), "seed": 0, "rate_per_s": args.serve_rate,
+    out = {"stream": {"requests": len(reqs), "seed": 0, "rate_per_s": rate,
+                      "batched_capacity_solves_per_s": capacity, "offered_load": rate / capacity,
                       "steps": [lo, hi], "sides": [64, 4096], "re": [1, 1e6],
                       "storages": ["f64", "f32", "f16"], "node_updates": work,
-                      "hbm_budget_gb": args.serve_budget_gb},
+                      "hbm_budget_gb": args.serve_budget_gb, "tuning_s_before_stream": tune_s,
+                      "fp64_requests_run_as": args.serve_fp64_as},
            "batched": S.summarize(res, srv.makespan, srv.node_updates),
            "precision_guard": {"stated_bounds": S.STATED_BOUND, "by_storage": gsum,
                                "finished_in": finished}}
@@ -298,16 +318,22 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100, help="time steps per end-to-end solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", default=None, help="override the lattice size, NXxNY")
-    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "vector"])
+    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16", "f64dw"])
+    ap.add_argument("--kernel", default="tuned", choices=["tuned", "auto", "scalar", "vector"],
+                    help="tuned: the autotuner picks the kernel shape per lattice (default)")
+    ap.add_argument("--tile-w", type=int, default=0, help="scalar kernel tile width (with --kernel scalar)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-serve-reference", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
-    ap.add_argument("--serve-rate", type=float, default=16.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="Poisson arrivals per second (0: serve-load x the measured batched capacity)")
+    ap.add_argument("--serve-load", type=float, default=1.2)
     ap.add_argument("--serve-scale", type=float, default=0.05,
                     help="step counts of the stream: [1000, 20000] x scale")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-fp64-as", default="f64dw", choices=["f64dw", "f64"],
+                    help="format the server runs FP64 requests in (the reference is always f64)")
     ap.add_argument("--mode", default="batch", choices=["batch", "single"],
                     help="batch: one launch per time step for all lattices; single: one per lattice")
     args = ap.parse_args()
@@ -341,11 +367,16 @@ def main():
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    from paper_2312_10318_gb300.tune import Tuner
+    tuner = Tuner(persist=False)      # measured afresh on this GPU, not cached on disk
     lats = []
     for pr in problems:
         lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode="lagged", stream=stream,
                       **pr.lattice_kwargs())
-        lat.set_kernel(args.kernel)
+        if args.kernel == "tuned":
+            tuner.apply(lat, pr.periodic, pr.mask is not None)
+        else:
+            lat.set_kernel(args.kernel, args.tile_w)
         lat.init(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
                    for a in (pr.ux, pr.uy, pr.rho)))
         lats.append(lat)
@@ -438,7 +469,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
             "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
                        "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
-                       "g_mode": "lagged", "kernel": [l.kernel()[0] and "vector" or "scalar" for l in lats][0],
+                       "g_mode": "lagged",
+                       "kernel": ("vector" if lats[0].kernel()[0] else f"scalar, tile {lats[0].kernel()[1]}")
+                                 + (" (autotuned)" if args.kernel == "tuned" else ""),
+                       "tuning": tuner.measured if args.kernel == "tuned" else None,
                        "parallelism": f"replicas x{world}",
                        "launch": "one batched kernel per time step" if args.mode == "batch"
                                  else "one kernel per lattice and time step",

@@ -43,11 +43,15 @@ extern "C" {
 
 /* Population storage formats.  All collision arithmetic of the reduced
  * formats runs in FP32 on the shifted deviation f_i - w_i rho0; FP64 storage
- * runs FP64 arithmetic. */
+ * runs FP64 arithmetic.  F64_DW is a 64-bit double-word format: each
+ * population is a pair of FP32 numbers hi + lo (~48 significant bits) and the
+ * collision runs in double-word FP32 arithmetic, which GB300 executes several
+ * times faster than its FP64 pipe; results agree with FP64 to ~1e-13. */
 #define TRTRLB_F64 0
 #define TRTRLB_F32 1
 #define TRTRLB_F16_SHIFTED 2
 #define TRTRLB_BF16_SHIFTED 3
+#define TRTRLB_F64_DW 4
 
 /* Time level of Phi_abg = rho u_a^3 delta... in the compensation term G_i
  * (eq_Gi).  The paper does not say which level; d_gamma Phi is a central
@@ -85,7 +89,7 @@ typedef struct {
     double rho0;             /* reference density of the shifted storage (> 0)   */
     double wall_ux, wall_uy; /* velocity of TRTRLB_INLET nodes                   */
     double wall_rho;         /* density rho_w in the moving-wall correction      */
-    int32_t storage;         /* TRTRLB_F64 | F32 | F16_SHIFTED | BF16_SHIFTED    */
+    int32_t storage;         /* TRTRLB_F64 | F32 | F16_SHIFTED | BF16_SHIFTED | F64_DW */
     int32_t g_mode;          /* TRTRLB_G_LAGGED | G_CURRENT | G_OFF              */
 } trtrlb_params;
 
@@ -177,13 +181,14 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
                                double* out, void* stream);
 
 /* Kernel shape of a lattice's step (the autotuner's knobs; results do not
- * depend on them).  variant: TRTRLB_KERNEL_AUTO (vector kernel whenever it
- * applies), TRTRLB_KERNEL_SCALAR (one node per thread), TRTRLB_KERNEL_VECTOR
+ * depend on them).  variant: TRTRLB_KERNEL_AUTO (the vector kernel where it
+ * applies for FP32/FP16/BF16, the scalar one for FP64 and F64_DW),
+ * TRTRLB_KERNEL_SCALAR (one node per thread), TRTRLB_KERNEL_VECTOR
  * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
  * lattice is periodic in both directions, has no mask and nx is a multiple
  * of that width).
- * tile_w: width in nodes of the scalar kernel's 256-thread tile in batches
- * (32, 64, 128 or 256; 0 keeps the current one). */
+ * tile_w: width in nodes of the scalar kernel's 256-thread tile (32, 64, 128
+ * or 256; 0 keeps the current one). */
 #define TRTRLB_KERNEL_AUTO 0
 #define TRTRLB_KERNEL_SCALAR 1
 #define TRTRLB_KERNEL_VECTOR 2

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtrtrlb.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
+F64, F32, F16_SHIFTED, BF16_SHIFTED, F64_DW = 0, 1, 2, 3, 4
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR = 0, 1, 2

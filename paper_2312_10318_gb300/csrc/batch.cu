@@ -68,6 +68,7 @@ int log2i(int v) {
     [&]() -> cudaError_t {                                                            \
         switch (storage) {                                                            \
             case TRTRLB_F64: { using S = double; return trt::Ops<S>::CALL; }          \
+            case TRTRLB_F64_DW: { using S = trt::f64dw; return trt::Ops<S>::CALL; }   \
             case TRTRLB_F32: { using S = float; return trt::Ops<S>::CALL; }           \
             case TRTRLB_F16_SHIFTED: { using S = __half; return trt::Ops<S>::CALL; }  \
             default: { using S = __nv_bfloat16; return trt::Ops<S>::CALL; }           \

@@ -60,6 +60,9 @@ template <> struct Fmt<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
 };
+}  // namespace trt
+#include "lb_dw.cuh"   // FP64 storage with double-word FP32 arithmetic (Fmt<f64dw>)
+namespace trt {
 
 // ---- kernel arguments -------------------------------------------------------
 template <typename C> struct Args {
@@ -160,7 +163,7 @@ template <typename C>
 __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k1lo,
                                         const C k2, const C k2lo, const C kf, const C gx,
                                         const C gy, const C rho0, C (&o)[9], C& phx, C& phy) {
-    const C third = C(1) / C(3);
+    const C third = C(1.0 / 3.0);
     // raw moments of the shifted populations
     const C s13 = d[1] + d[3], m13 = d[1] - d[3];
     const C s24 = d[2] + d[4], m24 = d[2] - d[4];

@@ -6,6 +6,9 @@
 
 namespace trt {
 
+// Storage tag of FP64 populations with double-word FP32 arithmetic (lb_dw.cuh).
+struct f64dw;
+
 // Threads per block of the diagnostics reduction.
 constexpr int DIAG_THREADS = 256;
 
@@ -29,7 +32,8 @@ struct State {
     long long plane;
     int px, py;
     bool general;         // walls, mask or non-periodic edges present
-    bool vec;             // the 128-bit vectorised kernel runs this lattice
+    bool vec;             // the vectorised kernel runs this lattice
+    int tile_w;           // scalar kernels: block of tile_w x (256 / tile_w) nodes
     int g_mode;
     double tau1, tau2, gx, gy, rho0;
     double wall_ux, wall_uy, wall_rho;

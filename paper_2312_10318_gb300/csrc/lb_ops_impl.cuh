@@ -38,7 +38,8 @@ static inline dim3 grid2d(const State& s, dim3 b) {
 
 template <typename S, bool ODD>
 static void launch_step(const State& s, const Args<typename Fmt<S>::C>& a, cudaStream_t st) {
-    const dim3 b(128, 2);
+    const int tw = s.tile_w > 0 ? s.tile_w : 128;
+    const dim3 b(tw, 256 / tw);
     const dim3 g = grid2d(s, b);
     if (s.general) {
         if (s.g_mode == G_OFF) k_step<S, ODD, true, G_OFF><<<g, b, 0, st>>>(a);

@@ -114,6 +114,35 @@ template <> struct Words<4> {
     }
 };
 
+// Double-word storage: packs of two (hi, lo) pairs in one float4.
+template <> struct Pk<f64dw> {
+    using P = float4;
+    using W = df64;
+    static constexpr int V = 2;
+    static __device__ __forceinline__ df64 get(const P& p, int v) {
+        return v == 0 ? df64(p.x, p.y) : df64(p.z, p.w);
+    }
+    static __device__ __forceinline__ void unpack2(const P& p, int, df64& a, df64& b) {
+        a = df64(p.x, p.y);
+        b = df64(p.z, p.w);
+    }
+    static __device__ __forceinline__ void pack2(P& p, int, df64 a, df64 b) {
+        p = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    static __device__ __forceinline__ W last_word(const P& p) { return df64(p.z, p.w); }
+    static __device__ __forceinline__ W first_word(const P& p) { return df64(p.x, p.y); }
+    static __device__ __forceinline__ W word_of(f64dw s) { return df64(s.hi, s.lo); }
+    static __device__ __forceinline__ P shift_up(const P& a, W prev) {
+        return make_float4(prev.hi, prev.lo, a.x, a.y);
+    }
+    static __device__ __forceinline__ P shift_down(const P& a, W next) {
+        return make_float4(a.z, a.w, next.hi, next.lo);
+    }
+    static __device__ __forceinline__ f64dw elem(const P& p, int v) {
+        return v == 0 ? f64dw{p.x, p.y} : f64dw{p.z, p.w};
+    }
+};
+
 // 2 NW x 16-bit elements in NW 32-bit words (element 2k: low half of word k).
 template <typename H, int NW> struct Pk16 {
     using WD = Words<NW>;
@@ -181,6 +210,14 @@ template <typename W>
 __device__ __forceinline__ W shfl_up1(W w) { return __shfl_up_sync(0xffffffffu, w, 1); }
 template <typename W>
 __device__ __forceinline__ W shfl_down1(W w) { return __shfl_down_sync(0xffffffffu, w, 1); }
+template <>
+__device__ __forceinline__ df64 shfl_up1<df64>(df64 w) {
+    return df64(__shfl_up_sync(0xffffffffu, w.hi, 1), __shfl_up_sync(0xffffffffu, w.lo, 1));
+}
+template <>
+__device__ __forceinline__ df64 shfl_down1<df64>(df64 w) {
+    return df64(__shfl_down_sync(0xffffffffu, w.hi, 1), __shfl_down_sync(0xffffffffu, w.lo, 1));
+}
 
 // Element I of a pack written to memory (storage format).
 template <typename S>

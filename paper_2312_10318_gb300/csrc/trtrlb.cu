@@ -22,13 +22,16 @@ thread_local char g_create_err[256] = "";
 size_t elem_size(int storage) {
     switch (storage) {
         case TRTRLB_F64: return sizeof(double);
+        case TRTRLB_F64_DW: return sizeof(double);
         case TRTRLB_F32: return sizeof(float);
         case TRTRLB_F16_SHIFTED: return sizeof(__half);
         case TRTRLB_BF16_SHIFTED: return sizeof(__nv_bfloat16);
         default: return 0;
     }
 }
-size_t phi_size(int storage) { return storage == TRTRLB_F64 ? sizeof(double) : sizeof(float); }
+size_t phi_size(int storage) {
+    return (storage == TRTRLB_F64 || storage == TRTRLB_F64_DW) ? 8 : sizeof(float);
+}
 
 int fail(char* buf, int code, const char* fmt, const char* detail = nullptr) {
     if (detail) std::snprintf(buf, 256, fmt, detail);
@@ -56,6 +59,7 @@ bool on_device(const void* p) {
     [&]() -> cudaError_t {                                                       \
         switch (storage) {                                                       \
             case TRTRLB_F64: { using S = double; return trt::Ops<S>::CALL; }     \
+            case TRTRLB_F64_DW: { using S = trt::f64dw; return trt::Ops<S>::CALL; } \
             case TRTRLB_F32: { using S = float; return trt::Ops<S>::CALL; }      \
             case TRTRLB_F16_SHIFTED: { using S = __half; return trt::Ops<S>::CALL; } \
             default: { using S = __nv_bfloat16; return trt::Ops<S>::CALL; }      \
@@ -72,6 +76,21 @@ void release(trtrlb_lattice* h) {
     if (h->part) cudaFree(h->part);
     if (h->dout) cudaFree(h->dout);
     delete h;
+}
+
+// The vector kernel needs a periodic lattice without mask and nx divisible
+// by its width.
+bool vector_applies(const trtrlb_lattice* h) {
+    return !h->s.general && h->p.nx % trt::vec_width((int)elem_size(h->p.storage)) == 0;
+}
+
+// Default kernel: the vector kernel for the 32- and 16-bit formats (measured
+// faster on GB300), the scalar one for the 64-bit formats (as fast for FP64,
+// faster for double-word storage, whose pairs double the vector kernel's
+// registers).  The autotuner may choose otherwise.
+bool auto_vector(const trtrlb_lattice* h) {
+    const int st = h->p.storage;
+    return vector_applies(h) && st != TRTRLB_F64 && st != TRTRLB_F64_DW;
 }
 
 // Staging buffer for host transfers (11 n doubles), allocated on first use.
@@ -143,7 +162,6 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
 
     const int pitch = (p.nx + 63) / 64 * 64;
     const long long plane = (long long)pitch * p.ny;
-    const long long n = (long long)p.nx * p.ny;
     std::vector<int> ghosts;
     if (mask) {
         for (int y = 0; y < p.ny; ++y)
@@ -235,8 +253,9 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     }
     h->t = 0;
     h->tile_w = p.nx >= 128 ? 128 : (p.nx >= 64 ? 64 : 32);
+    s.tile_w = h->tile_w;
     h->variant = TRTRLB_KERNEL_AUTO;
-    s.vec = !s.general && p.nx % trt::vec_width((int)es) == 0;
+    s.vec = auto_vector(h);
     *out = h;
     return TRTRLB_OK;
 }
@@ -388,10 +407,10 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
     h->err[0] = 0;
     if (tile_w != 0 && tile_w != 32 && tile_w != 64 && tile_w != 128 && tile_w != 256)
         return fail(h->err, TRTRLB_EINVAL, "tile_w must be 0, 32, 64, 128 or 256");
-    const bool can_vec = !h->s.general && h->p.nx % trt::vec_width((int)elem_size(h->p.storage)) == 0;
+    const bool can_vec = vector_applies(h);
     bool vec;
     switch (variant) {
-        case TRTRLB_KERNEL_AUTO: vec = can_vec; break;
+        case TRTRLB_KERNEL_AUTO: vec = auto_vector(h); break;
         case TRTRLB_KERNEL_SCALAR: vec = false; break;
         case TRTRLB_KERNEL_VECTOR:
             if (!can_vec)
@@ -403,7 +422,7 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
     }
     h->variant = variant;
     h->s.vec = vec;
-    if (tile_w) h->tile_w = tile_w;
+    if (tile_w) h->tile_w = h->s.tile_w = tile_w;
     return TRTRLB_OK;
 }
 

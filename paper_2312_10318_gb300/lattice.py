@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib
 
-STORAGE = {"f64": _lib.F64, "f32": _lib.F32, "f16": _lib.F16_SHIFTED, "bf16": _lib.BF16_SHIFTED}
+STORAGE = {"f64": _lib.F64, "f32": _lib.F32, "f16": _lib.F16_SHIFTED, "bf16": _lib.BF16_SHIFTED,
+           "f64dw": _lib.F64_DW}
 G_MODE = {"lagged": _lib.G_LAGGED, "current": _lib.G_CURRENT, "off": _lib.G_OFF}
 
 
@@ -54,7 +55,8 @@ class Lattice:
     periodic: (x, y); a non-periodic direction has stationary half-way
     bounce-back walls just outside the domain.  g: body acceleration (F = rho
     g).  mask: [ny, nx] uint8 of node classes (0 fluid, 1 solid, 2 inlet, 3
-    outlet ghost) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16'.
+    outlet ghost) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16' | 'f64dw' (FP64
+    storage, double-word FP32 arithmetic).
     g_mode: 'lagged' | 'off'.  stream: a torch.cuda.Stream or raw handle
     (default: the current torch stream).
     """

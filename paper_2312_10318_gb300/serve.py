@@ -27,7 +27,7 @@ from . import params as P
 from . import workloads as W
 
 KINDS = ("taylor_green", "double_shear_layer", "poiseuille")
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f64dw": 8}
 
 
 @dataclass
@@ -68,7 +68,7 @@ def lattice_bytes(n_x: int, n_y: int, storage: str) -> int:
     (9 per node), two Phi buffers of two components, the diagnostics scratch."""
     pitch = (n_x + 63) // 64 * 64
     plane = pitch * n_y
-    phi = 8 if storage == "f64" else 4
+    phi = 8 if storage in ("f64", "f64dw") else 4
     blocks = max(1, min(1216, -(-n_x * n_y // 256)))
     return 9 * STORAGE_BYTES[storage] * plane + 4 * phi * plane + 8 * 8 * blocks + 64
 
@@ -165,7 +165,7 @@ def device_fields(req: Request, pr, device="cuda"):
 # Stated end-of-run velocity error (relative L2 of u against FP64 storage,
 # eq_n1) per storage format: measured on the Taylor-Green vortex (64^2, u0 =
 # 0.04, Re = 100, 1000 steps: FP32 1.0e-5, FP16 6.1e-3, BF16 8.1e-2) with margin.
-STATED_BOUND = {"f64": 0.0, "f32": 1e-4, "f16": 1e-2, "bf16": 1e-1}
+STATED_BOUND = {"f64": 0.0, "f64dw": 0.0, "f32": 1e-4, "f16": 1e-2, "bf16": 1e-1}
 
 
 def l2(a, b) -> float:
@@ -225,7 +225,7 @@ class PrecisionGuard:
 
     def __call__(self, req: Request, lat):
         from .lattice import Lattice
-        if req.storage == "f64":
+        if lat.storage in ("f64", "f64dw"):
             return lat
         m = max(2, min(self.probe, req.steps // 16)) // 2 * 2
         sp = spec_of(req)
@@ -280,11 +280,16 @@ class Server:
     callable(request, lattice, status) run before a finished lattice is freed
     (to fetch fields).  max_active_nodes: admission stops while the admitted
     lattices hold this many nodes (the GPU is bandwidth-saturated well below
-    it), so requests finish closer to arrival order."""
+    it), so requests finish closer to arrival order.  tuner: optional
+    tune.Tuner whose kernel shapes are applied to every admitted lattice.
+    fp64_as: "f64dw" runs FP64 requests in the 64-bit double-word format (FP32
+    pairs, ~48-bit arithmetic; agrees with FP64 within the FP64 parity
+    tolerance and runs ~4x faster on GB300), "f64" in native FP64."""
 
     def __init__(self, hbm_budget: float = 150e9, chunk: int = 512, check_every: int = 8,
                  guard: Optional[Callable] = None, max_u: float = 0.5, stream=None,
-                 on_retire: Optional[Callable] = None, max_active_nodes: float = 48e6):
+                 on_retire: Optional[Callable] = None, max_active_nodes: float = 48e6,
+                 tuner=None, fp64_as: str = "f64"):
         import torch
         from .lattice import Batch
         self.stream = stream if stream is not None else torch.cuda.Stream()
@@ -296,6 +301,8 @@ class Server:
         self.max_u = max_u
         self.on_retire = on_retire    # callable(request, lattice, status) before a lattice is freed
         self.max_active_nodes = float(max_active_nodes)
+        self.tuner = tuner            # autotuner applied to every admitted lattice
+        self.fp64_as = fp64_as        # format FP64 requests run in: "f64" or "f64dw"
         self.active_nodes = 0
         self.used = 0
         self.node_updates = 0
@@ -304,7 +311,8 @@ class Server:
     def _admit(self, req: Request, now: float) -> Optional[_Active]:
         import torch
         from .lattice import Lattice
-        nbytes = lattice_bytes(req.n, req.n, req.storage)
+        storage = self.fp64_as if req.storage == "f64" else req.storage
+        nbytes = lattice_bytes(req.n, req.n, storage)
         if self.used + nbytes > self.budget:
             return None
         # enough nodes in flight saturate HBM; admitting more only stretches
@@ -315,11 +323,11 @@ class Server:
         # fields and init on the server's stream: the fields' memory is then
         # stream-ordered with the kernels that read it
         with torch.cuda.stream(self.stream):
-            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=req.storage, stream=self.stream,
+            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, stream=self.stream,
                           **pr.lattice_kwargs())
             ux, uy, rho = device_fields(req, pr)
             lat.init(ux, uy, rho)
-            act = _Active(req, lat, req.steps, now, nbytes, req.storage)
+            act = _Active(req, lat, req.steps, now, nbytes, storage)
             if self.guard is not None:
                 lat2 = self.guard(req, lat)
                 if lat2 is not lat:
@@ -328,6 +336,8 @@ class Server:
                     act.nbytes = lattice_bytes(req.n, req.n, lat2.storage)
                     lat.close()
                     act.lat = lat2
+            if self.tuner is not None:
+                self.tuner.apply(act.lat, pr.periodic)
         self.used += act.nbytes
         self.active_nodes += req.n * req.n
         return act
@@ -360,7 +370,7 @@ class Server:
             # admission, first come first served
             while waiting:
                 req = waiting[0]
-                if lattice_bytes(req.n, req.n, req.storage) > self.budget:
+                if lattice_bytes(req.n, req.n, self.fp64_as if req.storage == "f64" else req.storage) > self.budget:
                     waiting.pop(0)
                     results.append(Result(req.rid, "rejected", req.storage, 0, {}, req.arrival, now, now))
                     continue
@@ -404,6 +414,16 @@ class Server:
                     self.batch.set([])
         self.makespan = clock()
         return sorted(results, key=lambda r: r.rid)
+
+
+def shapes_of(requests: list, storages=None) -> set:
+    """Distinct (storage, nx, ny, periodic, has_mask) of a stream, for tuning."""
+    out = set()
+    for r in requests:
+        sp = spec_of(r)
+        for st in (storages or (r.storage,)):
+            out.add((st, sp.nx, sp.ny, sp.periodic, False))
+    return out
 
 
 def run_fifo(requests: list, storage: str = "f64", realtime: bool = True) -> list:

@@ -28,14 +28,18 @@ def _random_problem(nx, ny, seed, periodic=(True, True), g=(0.0, 0.0), mask=None
                      wall_u=wall_u, wall_rho=1.0)
 
 
+FP64 = ["f64", "f64dw"]   # FP64 storage: FP64 arithmetic, double-word FP32 arithmetic
+
+
+@pytest.mark.parametrize("storage", FP64)
 @pytest.mark.parametrize("nx,ny", SIZES)
 @pytest.mark.parametrize("g_mode", ["lagged", "off"])
 @pytest.mark.parametrize("periodic", [(True, True), (True, False), (False, True), (False, False)])
-def test_random_state_steps_match_oracle(gpu_lib, nx, ny, g_mode, periodic):
+def test_random_state_steps_match_oracle(gpu_lib, nx, ny, g_mode, periodic, storage):
     """Far-from-equilibrium random populations: 1, 2 and 5 steps (both AA parities)."""
     pr = _random_problem(nx, ny, seed=nx * 31 + ny, periodic=periodic, g=(1e-4, -5e-5))
     f0 = W.random_populations(nx, ny, seed=nx + 7 * ny)
-    G = gpu_lattice(pr, "f64", g_mode).set_f(f0)
+    G = gpu_lattice(pr, storage, g_mode).set_f(f0)
     R = oracle_lattice(pr, g_mode).set_f(f0)
     for n in (1, 1, 3):
         G.step(n)
@@ -44,15 +48,16 @@ def test_random_state_steps_match_oracle(gpu_lib, nx, ny, g_mode, periodic):
         assert max(errs.values()) < 1e-12, errs
 
 
+@pytest.mark.parametrize("storage", FP64)
 @pytest.mark.parametrize("seed", range(4))
-def test_masks_inlet_outlet_match_oracle(gpu_lib, seed):
+def test_masks_inlet_outlet_match_oracle(gpu_lib, seed, storage):
     """Random solid nodes, a moving-wall inlet column and a zero-gradient outlet."""
     nx, ny = 37, 23
     mask = W.random_mask(nx, ny, seed=seed, solid_frac=0.12, inlet_outlet=True)
     pr = _random_problem(nx, ny, seed=100 + seed, periodic=(False, seed % 2 == 0), g=(2e-5, 1e-5),
                          mask=mask, wall_u=(0.03, 0.005))
     rho, ux, uy = W.random_fields(nx, ny, seed=seed)
-    G = gpu_lattice(pr, "f64").init(ux, uy, rho)
+    G = gpu_lattice(pr, storage).init(ux, uy, rho)
     R = oracle_lattice(pr).init(ux, uy, rho)
     fluid = mask == O.FLUID
     for n in (1, 1, 10, 37):
@@ -67,13 +72,14 @@ def test_masks_inlet_outlet_match_oracle(gpu_lib, seed):
     assert d["wall_force_y"] == pytest.approx(fy, rel=1e-12, abs=1e-15)
 
 
+@pytest.mark.parametrize("storage", FP64)
 @pytest.mark.parametrize("variant", ["magic", "rlb"])
-def test_taylor_green_1000_steps_fp64(gpu_lib, variant):
+def test_taylor_green_1000_steps_fp64(gpu_lib, variant, storage):
     """64^2 Taylor-Green, u0 = 0.04, Re = 100, Lambda = 1/4 or tau2 = tau1: every
     field within 1e-10 of the oracle after 1000 steps."""
     pr = W.taylor_green(64, 0.04, 100.0, magic=0.25) if variant == "magic" else \
         W.taylor_green(64, 0.04, 100.0, tau_s2=P.tau_from_reynolds(100.0, 0.04, 64))
-    G = gpu_lattice(pr, "f64").init(pr.ux, pr.uy, pr.rho)
+    G = gpu_lattice(pr, storage).init(pr.ux, pr.uy, pr.rho)
     R = oracle_lattice(pr).init(pr.ux, pr.uy, pr.rho)
     G.step(1)
     R.step(1)
@@ -84,8 +90,9 @@ def test_taylor_green_1000_steps_fp64(gpu_lib, variant):
     assert max(errs.values()) < 1e-10, errs
 
 
+@pytest.mark.parametrize("storage", FP64)
 @pytest.mark.parametrize("tau1,magic", [(0.6, 1 / 12), (0.6, 3 / 16), (1.0, 1 / 4), (5.0, 1 / 2), (50.0, 3 / 16)])
-def test_poiseuille_steady_profile_fp64(gpu_lib, tau1, magic):
+def test_poiseuille_steady_profile_fp64(gpu_lib, tau1, magic, storage):
     """NX = 8 channel with half-way walls: the GPU steady state is the closed form of
     eq_a3 plus the slip of eq_a28, and matches the oracle."""
     ny, u_c = 32, 0.01
@@ -96,7 +103,7 @@ def test_poiseuille_steady_profile_fp64(gpu_lib, tau1, magic):
     y = np.arange(1, ny + 1) - 0.5
     exact = 4 * u_c / ny ** 2 * y * (ny - y) + us
     pr = W.poiseuille(ny, tau1, magic, nx=8, u_c=u_c, profile=exact)
-    G = gpu_lattice(pr, "f64").init(pr.ux, pr.uy)
+    G = gpu_lattice(pr, storage).init(pr.ux, pr.uy)
     R = oracle_lattice(pr).init(pr.ux, pr.uy)
     G.step(200)
     R.step(200)
@@ -109,11 +116,12 @@ def test_poiseuille_steady_profile_fp64(gpu_lib, tau1, magic):
     assert np.abs(uy).max() < 1e-9 * u_c
 
 
-def test_full_size_double_shear_layer_fp64_steps(gpu_lib):
+@pytest.mark.parametrize("storage", FP64)
+def test_full_size_double_shear_layer_fp64_steps(gpu_lib, storage):
     """Double shear layer 1024^2 (the benchmark's lattice) in FP64 storage: two steps
     element by element against the oracle over the whole lattice."""
     pr = W.double_shear_layer(1024, re=1e5)
-    G = gpu_lattice(pr, "f64").init(pr.ux, pr.uy)
+    G = gpu_lattice(pr, storage).init(pr.ux, pr.uy)
     R = oracle_lattice(pr).init(pr.ux, pr.uy)
     G.step(2)
     R.step(2)

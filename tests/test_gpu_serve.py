@@ -129,3 +129,18 @@ def test_precision_guard_falls_back_to_fp64(gpu_lib):
     mid = S.PrecisionGuard(tol=1e-4, probe=16)
     res = S.Server(chunk=64, guard=mid).run(reqs[:1], realtime=False)
     assert res[0].fallback and res[0].storage == "f32"
+
+
+def test_fp64_requests_in_double_word_format(gpu_lib):
+    """With fp64_as="f64dw" the FP64 requests run in the 64-bit double-word format
+    and agree with native FP64 solves within the FP64 parity tolerance."""
+    reqs = _small_stream(4, seed=13, storages=("f64",))
+    final = {}
+    srv = S.Server(chunk=64, fp64_as="f64dw",
+                   on_retire=lambda r, lat, st: final.__setitem__(r.rid, lat.get_f()))
+    res = srv.run(reqs, realtime=False)
+    assert all(r.storage == "f64dw" and r.status == "ok" for r in res)
+    for req in reqs:
+        (f64, _), _ = _alone(req)
+        rel = np.abs(final[req.rid] - f64).max() / np.abs(f64).max()
+        assert rel < 1e-11, (req, rel)

@@ -1,0 +1,35 @@
+"""The autotuner measures, caches and applies kernel shapes; results do not
+depend on the shape chosen."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2312_10318_gb300 import tune as T
+from paper_2312_10318_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tuner_measures_caches_and_applies(gpu_lib, tmp_path):
+    from paper_2312_10318_gb300 import Lattice
+    path = str(tmp_path / "tune.json")
+    t = T.Tuner(cache_path=path, steps=32, reps=2)
+    v, tw = t.choose("f32", 256, 256)
+    assert v in ("scalar", "vector") and tw in (0, 32, 64, 128, 256)
+    v2, _ = t.choose("f64dw", 128, 64, (True, False))
+    assert v2 == "scalar"                         # walls: only scalar kernels apply
+    data = json.load(open(path))
+    assert set(data) == {"f32/periodic/256x256", "f64dw/general/128x64"}
+    assert all(x > 0 for x in data["f32/periodic/256x256"]["candidates"].values())
+    # a second tuner reuses the cache without measuring
+    t2 = T.Tuner(cache_path=path)
+    assert t2.choose("f32", 250, 260) == (v, tw) and not t2.measured
+    # applying a shape does not change the state (FP32: bit-identical)
+    pr = W.taylor_green(256, 0.04, 300.0)
+    a = Lattice(256, 256, pr.tau_s, tau_s2=pr.tau_s2, storage="f32").set_kernel("scalar", 64)
+    b = Lattice(256, 256, pr.tau_s, tau_s2=pr.tau_s2, storage="f32")
+    t.apply(b)
+    for lat in (a, b):
+        lat.init(pr.ux, pr.uy, pr.rho).step(37)
+    assert np.array_equal(a.get_f(), b.get_f())

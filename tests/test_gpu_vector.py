@@ -14,7 +14,7 @@ from paper_2312_10318_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-V = {"f64": 2, "f32": 4, "f16": 4, "bf16": 4}
+V = {"f64": 2, "f32": 4, "f16": 4, "bf16": 4, "f64dw": 2}
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
 ULP = {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}
 TINY = {"f16": 2.0 ** -23, "bf16": 1e-30}   # FP16 subnormal spacing is 2^-24
@@ -25,7 +25,7 @@ def _same(storage, fa, fb, pa, pb, steps=1):
     states every population is within one rounding of the format; over `steps`
     steps the differences may propagate, bounded by `steps` roundings of the
     largest stored deviation."""
-    if storage in ("f64", "f32"):
+    if storage in ("f64", "f32", "f64dw"):
         return np.array_equal(fa, fb) and np.array_equal(pa, pb)
     da, db = fa - W9, fb - W9          # stored deviations (rho0 = 1)
     u = ULP[storage]
@@ -53,7 +53,7 @@ def _widths(storage):
     return sorted({v, 2 * v, 31 * v, 32 * v, 33 * v, 64 * v + v, 1024})
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "f64dw"])
 @pytest.mark.parametrize("g_mode", ["lagged", "off"])
 def test_vector_equals_scalar(gpu_lib, storage, g_mode):
     for k, nx in enumerate(_widths(storage)):
