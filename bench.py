@@ -80,7 +80,8 @@ def _rect(p, nx, ny):
 
 def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
     """Algorithmic bytes of one node update: 9 populations read and written, plus
-    (lagged G) two Phi values read and two written."""
+    (lagged G) two Phi values read and two written; the current-Phi kernel
+    computes Phi on chip and moves populations only."""
     b = 2 * 9 * STORAGE_BYTES[storage]
     if g_mode == "lagged":
         b += 4 * PHI_BYTES[storage]
@@ -322,6 +323,8 @@ def main():
     ap.add_argument("--kernel", default="tuned", choices=["tuned", "auto", "scalar", "vector"],
                     help="tuned: the autotuner picks the kernel shape per lattice (default)")
     ap.add_argument("--tile-w", type=int, default=0, help="scalar kernel tile width (with --kernel scalar)")
+    ap.add_argument("--g-mode", default="lagged", choices=["lagged", "current", "off"],
+                    help="time level of Phi in G_i: lagged (in-place kernels) or current (two-buffer kernel)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-serve-reference", action="store_true")
@@ -371,9 +374,9 @@ def main():
     tuner = Tuner(persist=False)      # measured afresh on this GPU, not cached on disk
     lats = []
     for pr in problems:
-        lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode="lagged", stream=stream,
+        lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode=args.g_mode, stream=stream,
                       **pr.lattice_kwargs())
-        if args.kernel == "tuned":
+        if args.kernel == "tuned" and args.g_mode != "current":
             tuner.apply(lat, pr.periodic, pr.mask is not None)
         else:
             lat.set_kernel(args.kernel, args.tile_w)
@@ -433,7 +436,7 @@ def main():
     per_step_launches = 1 if args.mode == "batch" else len(lats)
     launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
-    per_launch_bytes = bytes_per_node(storage) * nodes / per_step_launches
+    per_launch_bytes = bytes_per_node(storage, args.g_mode) * nodes / per_step_launches
     achieved = per_launch_bytes / launch_s / 1e9
     peak, peak_kind = hbm_peak()
     traffic = recorded_traffic(args.workload)
@@ -469,7 +472,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
             "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
                        "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
-                       "g_mode": "lagged",
+                       "g_mode": args.g_mode,
                        "kernel": ("vector" if lats[0].kernel()[0] else f"scalar, tile {lats[0].kernel()[1]}")
                                  + (" (autotuned)" if args.kernel == "tuned" else ""),
                        "tuning": tuner.measured if args.kernel == "tuned" else None,
@@ -483,7 +486,7 @@ def main():
                          "traffic": None if traffic is None else traffic,
                          "kernel": "trt::k_step_batch (fused AA stream-collide, all lattices)"
                                    if args.mode == "batch" else "trt::k_step (fused AA stream-collide)",
-                         "algorithmic_bytes_per_node": bytes_per_node(storage),
+                         "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode),
                          "launch_ms": launch_s * 1e3},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": field_bytes / args.e2e_steps,

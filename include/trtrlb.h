@@ -57,8 +57,10 @@ extern "C" {
  * (eq_Gi).  The paper does not say which level; d_gamma Phi is a central
  * difference over neighbouring nodes.
  *   LAGGED : Phi from the previous step (Phi^{-1} := Phi^0), used by the
- *            in-place AA kernel, which cannot see neighbours' current moments.
- *   CURRENT: Phi of the current step (two-pass reference semantics).
+ *            in-place AA kernels, which cannot see neighbours' current moments.
+ *   CURRENT: Phi of the current step, by the two-buffer kernel (Phi of each
+ *            tile and its halo computed in shared memory; twice the
+ *            population memory, no Phi traffic).
  *   OFF    : G_i = 0. */
 #define TRTRLB_G_LAGGED 0
 #define TRTRLB_G_CURRENT 1
@@ -106,7 +108,7 @@ void trtrlb_default_params(trtrlb_params* p);
  *   out    : receives the handle; unchanged on error.
  * The populations start at rest with density rho0.  Errors: EINVAL (bad size,
  * tau, magic/tau_s2, storage, mask class, outlet without a fluid inward
- * neighbour), ENOTSUP (G_CURRENT with the in-place kernel), ENOMEM, ECUDA. */
+ * neighbour), ENOMEM, ECUDA. */
 int trtrlb_create(const trtrlb_params* p, const uint8_t* mask, void* stream, trtrlb_t* out);
 
 /* Frees all memory of the handle (synchronises its stream).  NULL is a no-op. */
@@ -131,7 +133,8 @@ int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy);
 
 /* Populations f_i(x, t) of the current state as 9*nx*ny FP64 values, and
  * optionally (phi != NULL) the previous-level Phi as 2*nx*ny values
- * (Phi_xxx then Phi_yyy).  Non-fluid nodes report 0 populations. */
+ * (Phi_xxx then Phi_yyy; LAGGED only, zeros otherwise).  Non-fluid nodes
+ * report 0 populations. */
 int trtrlb_get_f(trtrlb_t h, double* f, double* phi);
 
 /* Replaces the populations of the current state (9*nx*ny FP64 values, rounded

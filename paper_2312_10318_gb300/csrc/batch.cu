@@ -54,6 +54,7 @@ std::vector<int> signature(const trtrlb_batch* b) {
     for (const trtrlb_lattice* h : b->lats) {
         sig.push_back(h->s.parity);
         sig.push_back(h->s.cur);
+        sig.push_back(h->s.f == h->f ? 0 : 1);   // two-buffer lattices alternate buffers
     }
     return sig;
 }
@@ -84,6 +85,7 @@ cudaError_t launch_steps(trtrlb_batch* b, int64_t n) {
         std::map<Key, std::vector<int>> groups;
         for (int i = 0; i < (int)b->lats.size(); ++i) {
             const trtrlb_lattice* h = b->lats[i];
+            if (h->s.g_mode == TRTRLB_G_CURRENT) continue;   // two-buffer kernel, below
             const int flav = h->s.general ? trt::FLAV_GENERAL : (h->s.vec ? trt::FLAV_VECTOR : trt::FLAV_PERIODIC);
             groups[Key{h->p.storage, flav, h->s.g_mode, h->s.parity ^ flip}].push_back(i);
         }
@@ -104,6 +106,11 @@ cudaError_t launch_steps(trtrlb_batch* b, int64_t n) {
             if (e != cudaSuccess) return e;
         }
         for (trtrlb_lattice* h : b->lats) {
+            if (h->s.g_mode == TRTRLB_G_CURRENT) {
+                const cudaError_t e = TRT_DISPATCH_S(h->p.storage, step_ab(h->s, flip, b->stream));
+                if (e != cudaSuccess) return e;
+                continue;
+            }
             if (h->s.nghost == 0) continue;
             const cudaError_t e = TRT_DISPATCH_S(h->p.storage, ghost_pass(h->s, flip, b->stream));
             if (e != cudaSuccess) return e;
@@ -188,8 +195,16 @@ int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps) {
     const cudaError_t e = launch_steps(b, nsteps - done);
     if (e != cudaSuccess) return cuda_fail(b, e, "batch step");
     for (trtrlb_lattice* h : b->lats) {
-        h->s.parity ^= (int)(nsteps & 1);
-        if (h->s.g_mode == TRTRLB_G_LAGGED) h->s.cur ^= (int)(nsteps & 1);
+        if (h->s.g_mode == TRTRLB_G_CURRENT) {
+            if (nsteps & 1) {
+                void* t = h->s.f;
+                h->s.f = h->s.f2;
+                h->s.f2 = t;
+            }
+        } else {
+            h->s.parity ^= (int)(nsteps & 1);
+            if (h->s.g_mode == TRTRLB_G_LAGGED) h->s.cur ^= (int)(nsteps & 1);
+        }
         h->t += nsteps;
     }
     return TRTRLB_OK;

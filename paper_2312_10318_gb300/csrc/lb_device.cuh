@@ -77,6 +77,7 @@ template <typename C> struct Args {
     C kf;                 // 1 - 1/(2 tau1)
     C gx, gy, rho0;
     C corr[9];            // moving-wall term 2 w_i rho_w (e_i.u_w) / c_s^2
+    C phin_x, phin_y;     // Phi of moving-wall (inlet) nodes, rho_w u_w^3
 };
 
 // Neighbourhood of node (x, y): wrapped coordinates and out-of-domain flags.

@@ -12,6 +12,7 @@ struct trtrlb_lattice {
     cudaStream_t stream;
     int64_t t;           // steps since init / set_f
     void* f;             // device allocations owned by the handle
+    void* f2;            // second population buffer (G_CURRENT only)
     void* phi;           // both Phi buffers in one allocation
     uint8_t* mask;
     int* ghosts;

@@ -23,6 +23,7 @@ inline int vec_width(int storage_bytes) { return storage_bytes == 2 ? VEC16_NODE
 // Format-independent description of a lattice's device state.
 struct State {
     void* f;              // populations, S[9][ny][pitch]
+    void* f2;             // second buffer of the two-buffer G_CURRENT kernel (else null)
     void* phi[2];         // Phi buffers, C[2][ny][pitch]
     int cur;              // phi[cur] holds the previous level
     const uint8_t* mask;  // device [ny][pitch] or nullptr
@@ -61,6 +62,9 @@ template <typename S> struct Ops {
     // Outlet-ghost pass after step index k of a sequence that started at the
     // state's current parity and Phi buffer.
     static cudaError_t ghost_pass(const State& s, int k, cudaStream_t st);
+    // Two-buffer G_CURRENT step q of a sequence starting from s.f (the buffers
+    // alternate with q); the caller swaps s.f / s.f2 after an odd count.
+    static cudaError_t step_ab(const State& s, int q, cudaStream_t st);
 };
 
 int diag_blocks(const State& s);

@@ -1,5 +1,6 @@
 // Definitions of Ops<S> (lb_ops.cuh); included once per storage format.
 #pragma once
+#include "lb_ab.cuh"
 #include "lb_aux.cuh"
 #include "lb_batch.cuh"
 #include "lb_ops.cuh"
@@ -29,6 +30,8 @@ static Args<C> make_args(const State& s, bool swap_phi = false) {
         const double eu = ex(i) * s.wall_ux + ey(i) * s.wall_uy;
         a.corr[i] = (C)(6.0 * wgt(i) * s.wall_rho * eu);
     }
+    a.phin_x = (C)(s.wall_rho * s.wall_ux * s.wall_ux * s.wall_ux);
+    a.phin_y = (C)(s.wall_rho * s.wall_uy * s.wall_uy * s.wall_uy);
     return a;
 }
 
@@ -61,8 +64,29 @@ static void launch_step_vec(const State& s, const Args<typename Fmt<S>::C>& a, c
 }
 
 template <typename S>
+cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
+    using C = typename Fmt<S>::C;
+    State v = s;
+    if (q & 1) {            // odd step of a sequence: the buffers have swapped
+        v.f = s.f2;
+        v.f2 = s.f;
+    }
+    const Args<C> a = make_args<C>(v);
+    const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
+    k_step_ab<S><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
+    return cudaGetLastError();
+}
+
+template <typename S>
 cudaError_t Ops<S>::step(State& s, cudaStream_t st) {
     using C = typename Fmt<S>::C;
+    if (s.g_mode == G_CURRENT) {
+        const cudaError_t e = step_ab(s, 0, st);
+        void* t = s.f;
+        s.f = s.f2;
+        s.f2 = t;
+        return e;
+    }
     const Args<C> a = make_args<C>(s);
     if (s.vec) {
         if (s.parity == 0) launch_step_vec<S, false>(s, a, st);

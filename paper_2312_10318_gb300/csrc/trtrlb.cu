@@ -69,6 +69,7 @@ bool on_device(const void* p) {
 void release(trtrlb_lattice* h) {
     if (!h) return;
     if (h->f) cudaFree(h->f);
+    if (h->f2) cudaFree(h->f2);
     if (h->phi) cudaFree(h->phi);
     if (h->mask) cudaFree(h->mask);
     if (h->ghosts) cudaFree(h->ghosts);
@@ -81,7 +82,8 @@ void release(trtrlb_lattice* h) {
 // The vector kernel needs a periodic lattice without mask and nx divisible
 // by its width.
 bool vector_applies(const trtrlb_lattice* h) {
-    return !h->s.general && h->p.nx % trt::vec_width((int)elem_size(h->p.storage)) == 0;
+    return !h->s.general && h->p.g_mode != TRTRLB_G_CURRENT &&
+           h->p.nx % trt::vec_width((int)elem_size(h->p.storage)) == 0;
 }
 
 // Default kernel: the vector kernel for the 32- and 16-bit formats (measured
@@ -152,9 +154,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     double tau2 = 0;
     if (int rc = resolve_tau2(p, &tau2, err)) return rc;
     if (elem_size(p.storage) == 0) return fail(err, TRTRLB_EINVAL, "unknown storage format");
-    if (p.g_mode == TRTRLB_G_CURRENT)
-        return fail(err, TRTRLB_ENOTSUP, "G_CURRENT is not built into the in-place AA kernel");
-    if (p.g_mode != TRTRLB_G_LAGGED && p.g_mode != TRTRLB_G_OFF)
+    if (p.g_mode != TRTRLB_G_LAGGED && p.g_mode != TRTRLB_G_OFF && p.g_mode != TRTRLB_G_CURRENT)
         return fail(err, TRTRLB_EINVAL, "unknown g_mode");
     if (!(p.rho0 > 0) || !std::isfinite(p.gx) || !std::isfinite(p.gy) ||
         !std::isfinite(p.wall_ux) || !std::isfinite(p.wall_uy) || !std::isfinite(p.wall_rho))
@@ -203,10 +203,12 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     };
     bool ok = alloc(&h->f, es * 9 * plane) && alloc(&h->phi, ps * 4 * plane) &&
               alloc((void**)&h->dout, sizeof(double) * 8);
+    if (ok && p.g_mode == TRTRLB_G_CURRENT) ok = alloc(&h->f2, es * 9 * plane);
     if (ok && mask) ok = alloc((void**)&h->mask, (size_t)plane);
     if (ok && !ghosts.empty()) ok = alloc((void**)&h->ghosts, sizeof(int) * ghosts.size());
     trt::State& s = h->s;
     s.f = h->f;
+    s.f2 = h->f2;
     s.phi[0] = h->phi;
     s.phi[1] = static_cast<char*>(h->phi) + ps * 2 * plane;
     s.cur = 0;
@@ -244,6 +246,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         }
     }
     e = cudaMemsetAsync(h->f, 0, es * 9 * plane, h->stream);
+    if (e == cudaSuccess && h->f2) e = cudaMemsetAsync(h->f2, 0, es * 9 * plane, h->stream);
     if (e == cudaSuccess) e = TRT_DISPATCH(p.storage, phi_static(h->s, h->stream));
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {

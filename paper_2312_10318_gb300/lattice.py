@@ -57,7 +57,7 @@ class Lattice:
     g).  mask: [ny, nx] uint8 of node classes (0 fluid, 1 solid, 2 inlet, 3
     outlet ghost) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16' | 'f64dw' (FP64
     storage, double-word FP32 arithmetic).
-    g_mode: 'lagged' | 'off'.  stream: a torch.cuda.Stream or raw handle
+    g_mode: 'lagged' | 'current' | 'off'.  stream: a torch.cuda.Stream or raw handle
     (default: the current torch stream).
     """
 

@@ -55,9 +55,6 @@ def test_create_rejects_invalid_parameters_before_touching_the_device(lib):
         assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL, field
     q = _lib.Params()
     C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
-    q.g_mode = _lib.G_CURRENT
-    assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.ENOTSUP
-    q.g_mode = _lib.G_LAGGED
     q.tau_s2, q.magic = 1.0, 0.3     # disagree with tau_s = 0.8
     assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL
     assert b"disagree" in lib.trtrlb_last_error(None)
