@@ -98,17 +98,31 @@ def hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the device-code sources (headers with the kernels and their
+    launch code, and the per-format instantiation units)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2312_10318_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2312_10318_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "lb_ops_*.cu"))):
         with open(p, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
+def kernel_label(args, vector: bool) -> str:
+    """Name of the step kernel the timed region launches."""
+    if args.g_mode == "current":
+        return "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)"
+    if args.mode == "batch":
+        return ("trt::k_step_group_vec" if vector else "trt::k_step_group") + \
+            " (fused AA stream-collide, all lattices in one launch)"
+    return ("trt::k_step_vec" if vector else "trt::k_step") + " (fused AA stream-collide)"
+
+
 def recorded_traffic(workload_name: str):
     """DRAM bytes per launch of the step kernel from a committed ncu summary, or None
-    when the kernel sources changed since that capture."""
-    pat = re.compile(r"^traffic_per_launch_bytes\[(\w+)\]:\s*([0-9.eE+]+)\s+source_hash:\s*(\w+)")
+    when the kernel sources changed since that capture.  workload_name is
+    '<workload>/<storage>/<g mode>'."""
+    pat = re.compile(r"^traffic_per_launch_bytes\[([\w/]+)\]:\s*([0-9.eE+]+)\s+source_hash:\s*(\w+)")
     for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         for line in open(p):
             m = pat.match(line.strip())
@@ -376,8 +390,9 @@ def main():
     for pr in problems:
         lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode=args.g_mode, stream=stream,
                       **pr.lattice_kwargs())
-        if args.kernel == "tuned" and args.g_mode != "current":
-            tuner.apply(lat, pr.periodic, pr.mask is not None)
+        if args.kernel == "tuned":
+            if args.g_mode != "current":     # the two-buffer kernel has one shape
+                tuner.apply(lat, pr.periodic, pr.mask is not None)
         else:
             lat.set_kernel(args.kernel, args.tile_w)
         lat.init(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
@@ -433,13 +448,14 @@ def main():
     value = nodes * args.steps * world / (total_ms / 1e3) / 1e6
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
-    per_step_launches = 1 if args.mode == "batch" else len(lats)
+    # the two-buffer (current-Phi) kernel runs one launch per lattice in a batch
+    per_step_launches = 1 if (args.mode == "batch" and args.g_mode != "current") else len(lats)
     launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
     per_launch_bytes = bytes_per_node(storage, args.g_mode) * nodes / per_step_launches
     achieved = per_launch_bytes / launch_s / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(f"{args.workload}/{storage}/{args.g_mode}") if args.mode == "batch" else None
 
     # end to end through the C ABI with pinned host buffers: init from host
     # fields, e2e_steps time steps, macroscopic fields back to host
@@ -484,8 +500,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic is None else traffic,
-                         "kernel": "trt::k_step_batch (fused AA stream-collide, all lattices)"
-                                   if args.mode == "batch" else "trt::k_step (fused AA stream-collide)",
+                         "kernel": kernel_label(args, lats[0].kernel()[0]),
                          "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode),
                          "launch_ms": launch_s * 1e3},
             "e2e": {"value": e2e_value, "unit": UNIT,

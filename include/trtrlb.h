@@ -83,7 +83,7 @@ typedef struct {
     int32_t periodic_y;      /*    just outside x = -1/2 and x = nx - 1/2 (y alike) */
     double tau_s;            /* tau_{s,1} > 1/2: relaxes the 1st and 2nd order;
                                 kinematic viscosity nu = (tau_s - 1/2)/3 (eq_mu) */
-    double tau_s2;           /* tau_{s,2} > 1/2: relaxes the 3rd order, or NaN   */
+    double tau_s2;           /* tau_{s,2} >= 1/2: relaxes the 3rd order, or NaN  */
     double magic;            /* Lambda_s = (tau_s - 1/2)(tau_s2 - 1/2) (eq_a29),
                                 or NaN.  Exactly one of tau_s2 / magic may be NaN;
                                 if both are given they must agree to 1e-12 rel. */

@@ -115,8 +115,10 @@ int resolve_tau2(const trtrlb_params& p, double* tau2, char* err) {
         if (std::fabs(from_m - t2) > 1e-12 * std::fabs(t2))
             return fail(err, TRTRLB_EINVAL, "tau_s2 and magic disagree");
     }
-    if (!(t2 > 0.5) || !std::isfinite(t2))
-        return fail(err, TRTRLB_EINVAL, "tau_s2 must be finite and > 1/2 (magic > 0)");
+    // tau_s2 = 1/2 (1/tau_s2 = 2, the end of the stability sweep of Sec. III A)
+    // mirrors the third-order non-equilibrium; below it the factor exceeds 1
+    if (!(t2 >= 0.5) || !std::isfinite(t2))
+        return fail(err, TRTRLB_EINVAL, "tau_s2 must be finite and >= 1/2 (magic >= 0)");
     *tau2 = t2;
     return 0;
 }

@@ -55,6 +55,9 @@ def test_create_rejects_invalid_parameters_before_touching_the_device(lib):
         assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL, field
     q = _lib.Params()
     C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+    q.tau_s2, q.magic = 0.4999, float("nan")     # tau_s2 = 1/2 is the smallest accepted
+    assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL
+    assert b">= 1/2" in lib.trtrlb_last_error(None)
     q.tau_s2, q.magic = 1.0, 0.3     # disagree with tau_s = 0.8
     assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL
     assert b"disagree" in lib.trtrlb_last_error(None)
