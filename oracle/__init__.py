@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+FLUID, SOLID, INLET, OUTLET, PRESSURE = 0, 1, 2, 3, 4
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 
 
@@ -28,6 +28,7 @@ class _Params(C.Structure):
         ("tau1", C.c_double), ("tau2", C.c_double),
         ("gx", C.c_double), ("gy", C.c_double),
         ("wall_ux", C.c_double), ("wall_uy", C.c_double), ("wall_rho", C.c_double),
+        ("outlet_rho", C.c_double),
         ("g_mode", C.c_int32),
     ]
 
@@ -47,11 +48,12 @@ class Params:
     wall_uy: float = 0.0
     wall_rho: float = 1.0
     g_mode: int = G_LAGGED
+    outlet_rho: float = 1.0
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, int(self.periodic_x), int(self.periodic_y),
                        self.tau1, self.tau2, self.gx, self.gy,
-                       self.wall_ux, self.wall_uy, self.wall_rho, self.g_mode)
+                       self.wall_ux, self.wall_uy, self.wall_rho, self.outlet_rho, self.g_mode)
 
 
 _LIB = None
@@ -84,6 +86,7 @@ def lib():
         L.orc_l2.argtypes = [_D, _D, C.c_int64]
         L.orc_l2.restype = C.c_double
         L.orc_drag.argtypes = [P, vp, _D, _D]
+        L.orc_zou_he.argtypes = [P, vp, _D]
         L.orc_num_threads.restype = C.c_int
         _LIB = L
     return _LIB
@@ -195,8 +198,10 @@ class Lattice:
         return self
 
     def set_f(self, f, phi=None):
-        """Sets the populations; Phi defaults to that of the new state."""
+        """Sets the populations (pressure outlet nodes rebuilt, reading R15); Phi
+        defaults to that of the new state."""
         self.f[...] = f
+        lib().orc_zou_he(C.byref(self.p.c()), _ptr(self.mask), self.f)
         if phi is None:
             lib().orc_phi_of_state(C.byref(self.p.c()), _ptr(self.mask), self.f, self.phi)
         else:
@@ -224,6 +229,14 @@ class Lattice:
         return out
 
 
+def zou_he(p: Params, mask, f) -> np.ndarray:
+    """The Zou-He rebuild of pressure outlet nodes (reading R15) applied to a
+    copy of the populations f [9, ny, nx]."""
+    out = np.ascontiguousarray(f, np.float64).copy()
+    lib().orc_zou_he(C.byref(p.c()), _ptr(_mask(p, mask)), out)
+    return out
+
+
 def l2(qn, qa) -> float:
     """Relative L2 error, eq_n1."""
     a = np.ascontiguousarray(qn, np.float64).ravel()
@@ -248,4 +261,4 @@ def viscosity(tau1: float) -> float:
 
 __all__ = ["Params", "Lattice", "lattice", "hermite", "equilibrium", "forcing", "compensation",
            "projections", "macroscopic", "collide_node", "l2", "num_threads", "tau2_from_magic", "viscosity",
-           "FLUID", "SOLID", "INLET", "OUTLET", "G_LAGGED", "G_CURRENT", "G_OFF"]
+           "zou_he", "FLUID", "SOLID", "INLET", "OUTLET", "PRESSURE", "G_LAGGED", "G_CURRENT", "G_OFF"]

@@ -39,6 +39,17 @@
  *       -2 w_i rho_w (e_i.u_w)/c_s^2 (e_i pointing into the wall); an outlet
  *       ghost node does not collide and re-emits the post-collision populations
  *       of its inward neighbour (x-1, y) (zero-gradient outlet).
+ *   R15 Zou-He constant-pressure outlet (Sec. III D): a class-4 node on the
+ *       last column of a lattice that is not periodic in x collides like a
+ *       fluid node; the populations entering it across the edge (e_x = -1)
+ *       are rebuilt from the others so that sum f = outlet_rho, sum e_y f = 0
+ *       and the normal non-equilibrium part bounces back:
+ *         f_i = f_ibar + (f^eq_i - f^eq_ibar)(outlet_rho, (u_x, 0))
+ *               - 1/2 e_iy (f_(0,1) - f_(0,-1)),
+ *       u_x = [sum_{e_x=0} f + 2 sum_{e_x=1} f] / outlet_rho - 1.  The rebuild
+ *       is applied to every state the step reads or returns.  Phi beyond the
+ *       edge is the outlet node's own value (zero gradient); the links that
+ *       leave across the edge are open, not walls.
  */
 #include <math.h>
 #include <stdint.h>
@@ -52,7 +63,7 @@
 #define ND 2
 
 /* Node classes of the boundary mask. */
-enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_INLET = 2, ORC_OUTLET = 3 };
+enum { ORC_FLUID = 0, ORC_SOLID = 1, ORC_INLET = 2, ORC_OUTLET = 3, ORC_PRESSURE = 4 };
 /* Time level of Phi in G_i (reading R1). */
 enum { ORC_G_LAGGED = 0, ORC_G_CURRENT = 1, ORC_G_OFF = 2 };
 
@@ -63,6 +74,7 @@ typedef struct {
     double tau2;      /* tau_{s,2}: relaxes the third order (eq2)        */
     double gx, gy;    /* body acceleration, F = rho g (eq_a2)            */
     double wall_ux, wall_uy, wall_rho; /* moving-wall state (inlet)      */
+    double outlet_rho; /* density of Zou-He pressure outlet nodes (R15)  */
     int32_t g_mode;   /* ORC_G_LAGGED / CURRENT / OFF                    */
 } orc_params;
 
@@ -260,21 +272,59 @@ static int cls(const uint8_t* mask, const orc_params* p, int x, int y) {
     return mask ? mask[node(p, x, y)] : ORC_FLUID;
 }
 
-/* Mask validity: classes in 0..3, and every outlet ghost's inward neighbour
- * (x-1, y) exists and is a fluid node.  Returns 0 when valid. */
+/* Nodes that collide: fluid nodes and pressure outlet nodes. */
+static int colliding(int c) { return c == ORC_FLUID || c == ORC_PRESSURE; }
+
+/* Mask validity: classes in 0..4, every outlet ghost's inward neighbour
+ * (x-1, y) exists and is a fluid node, and pressure outlet nodes lie on the
+ * last column of a lattice that is not periodic in x.  Returns 0 when valid. */
 int orc_check_mask(const orc_params* p, const uint8_t* mask) {
     if (!mask) return 0;
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             int c = mask[node(p, x, y)];
-            if (c > ORC_OUTLET) return 1;
+            if (c > ORC_PRESSURE) return 1;
             if (c == ORC_OUTLET) {
                 int xs = x - 1, ys = y;
                 if (!wrap(p, &xs, &ys) || cls(mask, p, xs, ys) != ORC_FLUID) return 2;
             }
+            if (c == ORC_PRESSURE && (p->periodic_x || x != p->nx - 1)) return 3;
         }
     return 0;
 }
+
+/* Zou-He rebuild (reading R15) of the populations entering every pressure
+ * outlet node across the x = nx edge, in place. */
+static void zou_he_outlet(const orc_params* p, const uint8_t* mask, double* f) {
+    if (!mask) return;
+    const size_t n = (size_t)p->nx * p->ny;
+    const int x = p->nx - 1;
+    for (int y = 0; y < p->ny; ++y) {
+        const size_t k = node(p, x, y);
+        if (mask[k] != ORC_PRESSURE) continue;
+        double fk[NQ];
+        for (int i = 0; i < NQ; ++i) fk[i] = f[(size_t)i * n + k];
+        double tangential = 0.0, outgoing = 0.0, fn = 0.0, fs = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+            if (EV[i][0] == 0) tangential += fk[i];
+            if (EV[i][0] == 1) outgoing += fk[i];
+            if (EV[i][0] == 0 && EV[i][1] == 1) fn = fk[i];
+            if (EV[i][0] == 0 && EV[i][1] == -1) fs = fk[i];
+        }
+        const double rho = p->outlet_rho;
+        const double u[ND] = {(tangential + 2.0 * outgoing) / rho - 1.0, 0.0};
+        double feq[NQ];
+        orc_equilibrium(rho, u, feq);
+        for (int i = 0; i < NQ; ++i) {
+            if (EV[i][0] != -1) continue;
+            const int j = opposite(i);
+            f[(size_t)i * n + k] = fk[j] + (feq[i] - feq[j]) - 0.5 * EV[i][1] * (fn - fs);
+        }
+    }
+}
+
+/* The rebuild on its own (for tests). */
+void orc_zou_he(const orc_params* p, const uint8_t* mask, double* f) { zou_he_outlet(p, mask, f); }
 
 /* Phi_xxx = rho u_x^3 and Phi_yyy = rho u_y^3 (eq_Gi) on every node, with
  * the non-fluid values of reading R2.  rho, ux, uy hold fluid-node moments. */
@@ -285,7 +335,7 @@ static void phi_field(const orc_params* p, const uint8_t* mask, const double* rh
         for (int x = 0; x < p->nx; ++x) {
             size_t k = node(p, x, y);
             int c = cls(mask, p, x, y);
-            if (c == ORC_FLUID) {
+            if (colliding(c)) {
                 phi[k] = rho[k] * ux[k] * ux[k] * ux[k];
                 phi[n + k] = rho[k] * uy[k] * uy[k] * uy[k];
             } else if (c == ORC_INLET) {
@@ -312,13 +362,23 @@ static double phi_at(const orc_params* p, const double* phi, int c, int x, int y
     return phi[(size_t)c * p->nx * p->ny + node(p, x, y)];
 }
 
+/* Phi component c at the neighbour (xn, yn) of node (x, y): beyond the edge
+ * next to a pressure outlet node it is that node's own value (reading R15). */
+static double phi_nb(const orc_params* p, const uint8_t* mask, const double* phi, int c, int x,
+                     int y, int xn, int yn) {
+    int xw = xn, yw = yn;
+    if (!wrap(p, &xw, &yw) && xn == p->nx && cls(mask, p, x, y) == ORC_PRESSURE)
+        return phi_at(p, phi, c, x, y);
+    return phi_at(p, phi, c, xn, yn);
+}
+
 /* Moments (eq11) of every fluid node; non-fluid nodes get rho = u = 0. */
 void orc_moments(const orc_params* p, const uint8_t* mask, const double* f, double* rho,
                  double* ux, double* uy) {
     const size_t n = (size_t)p->nx * p->ny;
     const double g[ND] = {p->gx, p->gy};
     for (size_t k = 0; k < n; ++k) {
-        if (mask && mask[k] != ORC_FLUID) {
+        if (mask && !colliding(mask[k])) {
             rho[k] = ux[k] = uy[k] = 0.0;
             continue;
         }
@@ -350,7 +410,7 @@ int orc_init(const orc_params* p, const uint8_t* mask, const double* rho, const 
     double* r = (double*)malloc(n * sizeof(double));
     for (size_t k = 0; k < n; ++k) {
         r[k] = rho ? rho[k] : 1.0;
-        if (mask && mask[k] != ORC_FLUID) {
+        if (mask && !colliding(mask[k])) {
             for (int i = 0; i < NQ; ++i) f[(size_t)i * n + k] = 0.0;
             continue;
         }
@@ -362,6 +422,7 @@ int orc_init(const orc_params* p, const uint8_t* mask, const double* rho, const 
             f[(size_t)i * n + k] = feq[i] - 0.5 * WV[i] * eF / CS2;
         }
     }
+    zou_he_outlet(p, mask, f);
     if (phi) phi_field(p, mask, r, ux, uy, phi);
     free(r);
     return 0;
@@ -386,6 +447,8 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
     double *rho = mom, *ux = mom + n, *uy = mom + 2 * n;
 
     for (int s = 0; s < nsteps; ++s) {
+        /* 0. pressure outlet populations of the state at time t (R15) */
+        zou_he_outlet(p, mask, f);
         /* 1. macroscopic fields at time t (eq11) */
         orc_moments(p, mask, f, rho, ux, uy);
         /* 2. Phi at time t (eq_Gi, reading R2) */
@@ -398,7 +461,7 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t k = node(p, x, y);
-                if (cls(mask, p, x, y) != ORC_FLUID) continue;
+                if (!colliding(cls(mask, p, x, y))) continue;
                 double fk[NQ], fs[NQ], dphi[ND * ND];
                 for (int i = 0; i < NQ; ++i) fk[i] = f[(size_t)i * n + k];
                 /* d_gamma Phi_{a b gamma}: Phi_{a b gamma} is rho u_a^3 when
@@ -412,8 +475,8 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
                                 if (!(a == b && b == c)) continue;
                                 int xp = x + (c == 0), yp = y + (c == 1);
                                 int xm = x - (c == 0), ym = y - (c == 1);
-                                d += 0.5 * (phi_at(p, phi_use, c, xp, yp) -
-                                            phi_at(p, phi_use, c, xm, ym));
+                                d += 0.5 * (phi_nb(p, mask, phi_use, c, x, y, xp, yp) -
+                                            phi_nb(p, mask, phi_use, c, x, y, xm, ym));
                             }
                         dphi[a * ND + b] = d;
                     }
@@ -428,7 +491,7 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 int c0 = cls(mask, p, x, y);
-                if (c0 != ORC_FLUID && c0 != ORC_OUTLET) continue;
+                if (!colliding(c0) && c0 != ORC_OUTLET) continue;
                 size_t k = node(p, x, y), ksrc = k;
                 if (c0 == ORC_OUTLET) {
                     int xs = x - 1, ys = y;
@@ -439,12 +502,14 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
                     double fs = fstar[(size_t)i * n + ksrc];
                     int xt = x + EV[i][0], yt = y + EV[i][1];
                     int inside = wrap(p, &xt, &yt);
+                    /* a pressure outlet's links across the edge are open */
+                    if (!inside && c0 == ORC_PRESSURE && EV[i][0] == 1) continue;
                     int ct = inside ? cls(mask, p, xt, yt) : ORC_SOLID;
-                    if (ct == ORC_FLUID) {
+                    if (colliding(ct)) {
                         fnew[(size_t)i * n + node(p, xt, yt)] = fs;
-                    } else if (c0 == ORC_FLUID && ct == ORC_SOLID) {
+                    } else if (colliding(c0) && ct == ORC_SOLID) {
                         fnew[(size_t)opposite(i) * n + k] = fs;
-                    } else if (c0 == ORC_FLUID && ct == ORC_INLET) {
+                    } else if (colliding(c0) && ct == ORC_INLET) {
                         double eu = EV[i][0] * p->wall_ux + EV[i][1] * p->wall_uy;
                         fnew[(size_t)opposite(i) * n + k] =
                             fs - 2.0 * WV[i] * p->wall_rho * eu / CS2;
@@ -454,6 +519,7 @@ int orc_step(const orc_params* p, const uint8_t* mask, double* f, double* phi, i
                 }
             }
         memcpy(f, fnew, (size_t)NQ * n * sizeof(double));
+        zou_he_outlet(p, mask, f);
         /* 5. LAGGED: Phi^t becomes the previous level of the next step */
         if (p->g_mode == ORC_G_LAGGED) memcpy(phi, phi_t, 2 * n * sizeof(double));
     }
@@ -489,10 +555,13 @@ void orc_drag(const orc_params* p, const uint8_t* mask, const double* f, double*
     force[0] = force[1] = 0.0;
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
-            if (cls(mask, p, x, y) != ORC_FLUID) continue;
+            const int c = cls(mask, p, x, y);
+            if (!colliding(c)) continue;
             for (int i = 1; i < NQ; ++i) {
                 int xt = x + EV[i][0], yt = y + EV[i][1];
-                if (wrap(p, &xt, &yt) && cls(mask, p, xt, yt) != ORC_SOLID) continue;
+                const int inside = wrap(p, &xt, &yt);
+                if (inside && cls(mask, p, xt, yt) != ORC_SOLID) continue;
+                if (!inside && c == ORC_PRESSURE && EV[i][0] == 1) continue;  /* open (R15) */
                 double fr = f[(size_t)opposite(i) * n + node(p, x, y)];
                 force[0] += 2.0 * EV[i][0] * fr;
                 force[1] += 2.0 * EV[i][1] * fr;

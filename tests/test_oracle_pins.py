@@ -436,6 +436,72 @@ def test_uniform_flow_through_inlet_and_outlet():
     assert np.abs(L.f[:, fluid] - f0[:, fluid]).max() < 1e-15
 
 
+def _pressure_lattice(nx=9, ny=6, seed=0, **kw):
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[:, nx - 1] = O.PRESSURE
+    return mask, O.Params(nx=nx, ny=ny, tau1=0.8, tau2=1.1, periodic_x=False, periodic_y=True, **kw)
+
+
+@pytest.mark.parametrize("rho_out", [1.0, 0.97])
+def test_zou_he_rebuild_conditions(rho_out):
+    """Reading R15 (Zou-He pressure outlet, Sec. III D): after the rebuild every
+    outlet node has sum f = rho_out, no transverse momentum, and the normal
+    populations differ as at equilibrium with u = (u_x, 0):
+    f_(1,0) - f_(-1,0) = 2 w_1 rho_out u_x / c_s^2 = (2/3) rho_out u_x.  Those
+    three conditions fix the three rebuilt populations; the others and every
+    other node are untouched, and rebuilding twice changes nothing."""
+    mask, p = _pressure_lattice(outlet_rho=rho_out)
+    f = W.random_populations(p.nx, p.ny, seed=3, amp=0.3)
+    g = O.zou_he(p, mask, f)
+    e, _, _ = O.lattice()
+    inflow = e[:, 0] == -1
+    out = mask == O.PRESSURE
+    assert np.array_equal(g[:, ~out], f[:, ~out])
+    assert np.array_equal(g[~inflow][:, out], f[~inflow][:, out])
+    assert not np.allclose(g[inflow][:, out], f[inflow][:, out])
+    rho = g[:, out].sum(axis=0)
+    jx = (e[:, 0, None] * g[:, out]).sum(axis=0)
+    jy = (e[:, 1, None] * g[:, out]).sum(axis=0)
+    assert np.abs(rho - rho_out).max() < 1e-15
+    assert np.abs(jy).max() < 1e-16
+    i1 = int(np.flatnonzero((e[:, 0] == 1) & (e[:, 1] == 0))[0])
+    i3 = int(np.flatnonzero((e[:, 0] == -1) & (e[:, 1] == 0))[0])
+    assert np.abs(g[i1, out] - g[i3, out] - (2.0 / 3.0) * jx).max() < 1e-16
+    assert np.array_equal(O.zou_he(p, mask, g), g)
+
+
+def test_pressure_outlet_placement_is_validated():
+    mask, p = _pressure_lattice()
+    bad = mask.copy()
+    bad[2, p.nx - 2] = O.PRESSURE
+    with pytest.raises(ValueError):
+        O.Lattice(p, mask=bad)
+    p.periodic_x = True
+    with pytest.raises(ValueError):
+        O.Lattice(p, mask=mask)
+
+
+@pytest.mark.parametrize("g_mode", [O.G_LAGGED, O.G_CURRENT, O.G_OFF])
+def test_uniform_flow_through_inlet_and_pressure_outlet(g_mode):
+    """A uniform stream at the outlet density entering through a moving-wall
+    inlet and leaving through the Zou-He outlet is an exact steady state: the
+    rebuild returns the equilibrium, the open links emit nothing back, and Phi
+    beyond the edge equals the outlet's own (a zero Phi there would give the
+    outlet a spurious d_x Phi and a non-zero G_i)."""
+    nx, ny, U = 10, 4, 0.05
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[:, 0] = O.INLET
+    mask[:, nx - 1] = O.PRESSURE
+    L = _lat(nx, ny, 0.7, 0.8, periodic_x=False, periodic_y=True, wall_ux=U, mask=mask,
+             g_mode=g_mode)
+    L.init(np.full((ny, nx), U), np.zeros((ny, nx)))
+    f0 = L.f.copy()
+    L.step(40)
+    live = mask != O.INLET
+    assert np.abs(L.f[:, live] - f0[:, live]).max() < 1e-15
+    assert np.abs(L.drag()).max() < 1e-13
+
+
 def test_taylor_green_decay_rate():
     """Sec. III B: the Taylor-Green velocity amplitude decays as exp(-2 nu k^2 t),
     nu = (tau1 - 1/2)/3 (eq_mu); the viscosity fitted over 1000 steps on 64^2 agrees
