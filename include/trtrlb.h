@@ -74,6 +74,16 @@ extern "C" {
 #define TRTRLB_OUTLET 3 /* zero-gradient outlet ghost: does not collide and
                            re-emits the post-collision populations of its
                            inward neighbour (x-1, y), which must be fluid    */
+#define TRTRLB_PRESSURE 4 /* Zou-He constant-pressure outlet (Sec. III D): a
+                           node on the last column x = nx-1 of a lattice not
+                           periodic in x; it collides like a fluid node after
+                           the populations entering across the edge (e_x < 0)
+                           are rebuilt so that rho = outlet_rho, u_y = 0 and
+                           the normal non-equilibrium parts bounce back.
+                           Links leaving across the edge are open; Phi beyond
+                           the edge is the node's own.  Every read of the
+                           state (step, moments, populations, diagnostics)
+                           sees the rebuilt values.                          */
 
 /* Problem statement (Sec. II B, eq2; eq_mu; eq_a2; eq_a29). */
 typedef struct {
@@ -91,6 +101,7 @@ typedef struct {
     double rho0;             /* reference density of the shifted storage (> 0)   */
     double wall_ux, wall_uy; /* velocity of TRTRLB_INLET nodes                   */
     double wall_rho;         /* density rho_w in the moving-wall correction      */
+    double outlet_rho;       /* density of TRTRLB_PRESSURE nodes (> 0)           */
     int32_t storage;         /* TRTRLB_F64 | F32 | F16_SHIFTED | BF16_SHIFTED | F64_DW */
     int32_t g_mode;          /* TRTRLB_G_LAGGED | G_CURRENT | G_OFF              */
 } trtrlb_params;
@@ -98,7 +109,7 @@ typedef struct {
 typedef struct trtrlb_lattice* trtrlb_t;
 
 /* Fills *p with defaults: periodic 64x64, tau_s = 0.8, magic = 1/4 (tau_s2 NaN),
- * no force, rho0 = wall_rho = 1, FP32 storage, LAGGED. */
+ * no force, rho0 = wall_rho = outlet_rho = 1, FP32 storage, LAGGED. */
 void trtrlb_default_params(trtrlb_params* p);
 
 /* Creates a lattice and allocates its device memory on the current device.
@@ -108,7 +119,8 @@ void trtrlb_default_params(trtrlb_params* p);
  *   out    : receives the handle; unchanged on error.
  * The populations start at rest with density rho0.  Errors: EINVAL (bad size,
  * tau, magic/tau_s2, storage, mask class, outlet without a fluid inward
- * neighbour), ENOMEM, ECUDA. */
+ * neighbour, pressure outlet off the last column or on a lattice periodic in
+ * x), ENOMEM, ECUDA. */
 int trtrlb_create(const trtrlb_params* p, const uint8_t* mask, void* stream, trtrlb_t* out);
 
 /* Frees all memory of the handle (synchronises its stream).  NULL is a no-op. */
@@ -166,6 +178,8 @@ int trtrlb_diagnostics(trtrlb_t h, double* out);
  *   f      : device, 9*nx*ny FP64 populations (layout above; e.g. what
  *            trtrlb_get_f writes), read only;
  *   mask   : device, nx*ny bytes of TRTRLB_* classes, or NULL (all fluid);
+ *            pressure outlet nodes count as fluid with f taken as given (a
+ *            state from trtrlb_get_f already holds the rebuilt values);
  *   periodic_x/y, gx, gy : as in trtrlb_params (u includes the g/2 shift);
  *   out    : device, 8 doubles, same meaning as in trtrlb_diagnostics;
  *   stream : cudaStream_t the two kernels run on (asynchronous).

@@ -30,6 +30,7 @@ class Params(C.Structure):
         ("gx", C.c_double), ("gy", C.c_double),
         ("rho0", C.c_double),
         ("wall_ux", C.c_double), ("wall_uy", C.c_double), ("wall_rho", C.c_double),
+        ("outlet_rho", C.c_double),
         ("storage", C.c_int32), ("g_mode", C.c_int32),
     ]
 

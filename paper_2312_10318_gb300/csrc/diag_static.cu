@@ -62,9 +62,10 @@ struct Canon {
 };
 
 // True when x + e_i is a stationary wall: a solid node, or outside a
-// non-periodic edge.
-__device__ __forceinline__ bool wall_link(const Canon& c, int x, int y, int i) {
+// non-periodic edge (except the open edge of a pressure outlet node).
+__device__ __forceinline__ bool wall_link(const Canon& c, int x, int y, int i, bool pressure) {
     int xn = x + trt::ex(i), yn = y + trt::ey(i);
+    if (pressure && trt::ex(i) > 0) return false;
     if (xn < 0 || xn >= c.nx) {
         if (!c.px) return true;
         xn = (xn + c.nx) % c.nx;
@@ -85,7 +86,8 @@ __global__ void __launch_bounds__(kThreads) k_diag_static_partial(Canon c, doubl
     for (int r = 0; r < kNodesPerThread; ++r) {
         const long long k = base + (long long)r * kThreads + threadIdx.x;
         if (k >= n) break;
-        if (c.mask && c.mask[k] != trt::FLUID) continue;
+        const int cls = c.mask ? c.mask[k] : trt::FLUID;
+        if (!trt::collides(cls)) continue;
         const int x = (int)(k % c.nx), y = (int)(k / c.nx);
         double f[9];
         bool finite = true;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_static_partial(Canon c, doubl
         acc[4] = fmax(acc[4], sqrt(ux * ux + uy * uy));
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            if (wall_link(c, x, y, i)) {
+            if (wall_link(c, x, y, i, cls == trt::PRESSURE)) {
                 acc[6] += 2.0 * trt::ex(i) * f[trt::opp(i)];
                 acc[7] += 2.0 * trt::ey(i) * f[trt::opp(i)];
             }

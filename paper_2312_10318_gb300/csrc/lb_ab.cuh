@@ -35,12 +35,19 @@ __device__ __forceinline__ int ab_class(const Args<C>& a, int& x, int& y) {
     return a.mask ? a.mask[(long long)y * a.pitch + x] : FLUID;
 }
 
-// Phi_xxx, Phi_yyy of node (x, y) of the canonical state (wall reading R2).
+// Phi_xxx, Phi_yyy of node (x, y) of the canonical state (wall reading R2;
+// beyond a pressure outlet node the outlet's own value).
 template <typename S>
 __device__ __forceinline__ void ab_phi(const Args<typename Fmt<S>::C>& a, const S* F, int x, int y,
                                        typename Fmt<S>::C& px, typename Fmt<S>::C& py) {
     using C = typename Fmt<S>::C;
+    const int x_in = x;
     int c = ab_class(a, x, y);
+    if (c == AB_OUT && x_in == a.nx && y >= 0 && y < a.ny && a.mask &&
+        a.mask[(long long)y * a.pitch + a.nx - 1] == PRESSURE) {
+        x = a.nx - 1;
+        c = PRESSURE;
+    }
     if (c == AB_OUT || c == SOLID) {
         px = py = C(0);
         return;
@@ -57,15 +64,20 @@ __device__ __forceinline__ void ab_phi(const Args<typename Fmt<S>::C>& a, const 
     C d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[(long long)i * a.plane + k]);
+    if (c == PRESSURE) zh_fill<C>(d, a.zh_dr);
     C rho, ux, uy;
     moments_of<C>(d, a.gx, a.gy, a.rho0, rho, ux, uy);
     px = rho * ux * ux * ux;
     py = rho * uy * uy * uy;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>::C> a, S* dst,
-                                                           int g_off) {
+__device__ __forceinline__ int ab_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// GENERAL: walls, masks or non-periodic edges; otherwise the lattice is
+// periodic in x and y without a mask and every link streams.
+template <typename S, bool GENERAL>
+__global__ void __launch_bounds__(AB_TX * AB_TY, 4) k_step_ab(Args<typename Fmt<S>::C> a, S* dst,
+                                                              int g_off) {
     using C = typename Fmt<S>::C;
     __shared__ C sx[AB_TY][AB_TX + 2];   // Phi_xxx with left/right halo
     __shared__ C sy[AB_TY + 2][AB_TX];   // Phi_yyy with top/bottom halo
@@ -76,11 +88,13 @@ __global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>:
     const bool inside = x < a.nx && y < a.ny;
 
     const long long own = (long long)y * a.pitch + x;
-    const bool fluid = inside && (!a.mask || a.mask[own] == FLUID);
+    const int cls = (GENERAL && a.mask && inside) ? a.mask[own] : FLUID;
+    const bool fluid = inside && collides(cls);
     C d[9];
     if (fluid) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[(long long)i * a.plane + own]);
+        if (GENERAL && cls == PRESSURE) zh_fill<C>(d, a.zh_dr);
     }
 
     // phase 1: Phi of the tile and its halo.  A shared cell holds Phi of its
@@ -89,7 +103,60 @@ __global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>:
     // tile's edge (the periodic neighbours of the last column and row), and
     // the halo column/row next to a full tile edge.  Every position computed is
     // within one node of the lattice, so one wrap brings it inside.
-    if (!g_off) {
+    if (!g_off && !GENERAL) {
+        // periodic lattice: every thread loads its halo node (if it has one)
+        // together with its own node, so the two load latencies overlap
+        const int h = (int)threadIdx.x;
+        int hx = -1, hy = -1;                     // wrapped halo position
+        if (h < 2 * AB_TY) {                      // left / right halo columns
+            const int r = h % AB_TY, side = h / AB_TY;
+            if (y0 + r < a.ny && (side ? x0 + AB_TX - 1 < a.nx : true)) {
+                hx = ab_wrap(side ? x0 + AB_TX : x0 - 1, a.nx);
+                hy = y0 + r;
+            }
+        } else if (h < 2 * AB_TY + 2 * AB_TX) {   // bottom / top halo rows
+            const int k = h - 2 * AB_TY;
+            const int c = k % AB_TX, side = k / AB_TX;
+            if (x0 + c < a.nx && (side ? y0 + AB_TY - 1 < a.ny : true)) {
+                hx = x0 + c;
+                hy = ab_wrap(side ? y0 + AB_TY : y0 - 1, a.ny);
+            }
+        }
+        // the cell just past a partial tile's last column / row
+        const bool past = !inside && ((x == a.nx && y < a.ny) || (y == a.ny && x < a.nx));
+        C e[9];
+        if (past) {
+            const long long k = (long long)ab_wrap(y, a.ny) * a.pitch + ab_wrap(x, a.nx);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[(long long)i * a.plane + k]);
+        }
+        if (hx >= 0) {
+            const long long k = (long long)hy * a.pitch + hx;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) e[i] = Fmt<S>::ld(F[(long long)i * a.plane + k]);
+        }
+        C px = C(0), py = C(0);
+        if (inside || past) {
+            C rho, ux, uy;
+            moments_of<C>(d, a.gx, a.gy, a.rho0, rho, ux, uy);
+            px = rho * ux * ux * ux;
+            py = rho * uy * uy * uy;
+        }
+        sx[ty][tx + 1] = px;
+        sy[ty + 1][tx] = py;
+        if (h < 2 * AB_TY + 2 * AB_TX) {
+            C qx = C(0), qy = C(0);
+            if (hx >= 0) {
+                C rho, ux, uy;
+                moments_of<C>(e, a.gx, a.gy, a.rho0, rho, ux, uy);
+                qx = rho * ux * ux * ux;
+                qy = rho * uy * uy * uy;
+            }
+            if (h < 2 * AB_TY) sx[h % AB_TY][h / AB_TY ? AB_TX + 1 : 0] = qx;
+            else sy[(h - 2 * AB_TY) / AB_TX ? AB_TY + 1 : 0][(h - 2 * AB_TY) % AB_TX] = qy;
+        }
+        __syncthreads();
+    } else if (!g_off) {
         C px = C(0), py = C(0);
         if (fluid) {
             C rho, ux, uy;
@@ -131,6 +198,19 @@ __global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>:
     }
     C o[9], phx, phy;
     collide<C>(d, dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
+    if (!GENERAL) {
+        const int xm = ab_wrap(x - 1, a.nx), xp = ab_wrap(x + 1, a.nx);
+        const long long rm = (long long)ab_wrap(y - 1, a.ny) * a.pitch;
+        const long long r0 = (long long)y * a.pitch;
+        const long long rp = (long long)ab_wrap(y + 1, a.ny) * a.pitch;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const long long row = ey(i) > 0 ? rp : (ey(i) < 0 ? rm : r0);
+            const int col = ex(i) > 0 ? xp : (ex(i) < 0 ? xm : x);
+            dst[(long long)i * a.plane + row + col] = Fmt<S>::st(o[i]);
+        }
+        return;
+    }
     // is (x, y) the inward neighbour of an outlet ghost?
     int gx = x + 1, gy = y;
     const bool proxy = a.mask && ab_class(a, gx, gy) == OUTLET;
@@ -138,9 +218,11 @@ __global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>:
     for (int i = 0; i < 9; ++i) {
         int txn = x + ex(i), tyn = y + ey(i);
         const int c = i == 0 ? FLUID : ab_class(a, txn, tyn);
-        if (c == FLUID) {
+        if (collides(c)) {
             dst[(long long)i * a.plane + (long long)tyn * a.pitch + txn] = Fmt<S>::st(o[i]);
         } else if (c == SOLID || c == AB_OUT) {
+            // (across the edge of a pressure outlet this fills a population
+            // that the Zou-He rebuild replaces when it is read)
             dst[(long long)opp(i) * a.plane + own] = Fmt<S>::st(o[i]);
         } else if (c == INLET) {
             dst[(long long)opp(i) * a.plane + own] = Fmt<S>::st(o[i] - a.corr[i]);
@@ -148,7 +230,7 @@ __global__ void __launch_bounds__(AB_TX * AB_TY) k_step_ab(Args<typename Fmt<S>:
         // links into an outlet ghost are dropped
         if (proxy && i != 0) {
             int sxn = gx + ex(i), syn = gy + ey(i);
-            if (ab_class(a, sxn, syn) == FLUID)
+            if (collides(ab_class(a, sxn, syn)))
                 dst[(long long)i * a.plane + (long long)syn * a.pitch + sxn] = Fmt<S>::st(o[i]);
         }
     }

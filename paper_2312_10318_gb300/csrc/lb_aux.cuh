@@ -17,7 +17,7 @@ __global__ void k_phi_static(const uint8_t* __restrict__ mask, int nx, int ny, i
     if (x >= nx || y >= ny) return;
     const long long k = (long long)y * pitch + x;
     const uint8_t c = mask ? mask[k] : FLUID;
-    if (c == FLUID || c == OUTLET) return;
+    if (collides(c) || c == OUTLET) return;
     const C vx = c == INLET ? inx : C(0), vy = c == INLET ? iny : C(0);
     phi0[k] = vx; phi0[plane + k] = vy;
     phi1[k] = vx; phi1[plane + k] = vy;
@@ -54,7 +54,7 @@ __global__ void k_init(Args<typename Fmt<S>::C> a, const double* __restrict__ rh
     S* F = static_cast<S*>(a.f);
     const long long own = (long long)y * a.pitch + x;
     const long long k = (long long)y * a.nx + x;
-    const bool fluid = !a.mask || a.mask[own] == FLUID;
+    const bool fluid = !a.mask || collides(a.mask[own]);
     if (!fluid) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) F[(long long)i * a.plane + own] = Fmt<S>::st(C(0));
@@ -88,7 +88,8 @@ __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, d
     const S* F = static_cast<const S*>(a.f);
     const long long own = (long long)y * a.pitch + x;
     const long long k = (long long)y * a.nx + x;
-    if (a.mask && a.mask[own] != FLUID) {
+    const int c = a.mask ? a.mask[own] : FLUID;
+    if (!collides(c)) {
         if (rho) rho[k] = 0.0;
         if (ux) ux[k] = 0.0;
         if (uy) uy[k] = 0.0;
@@ -100,6 +101,7 @@ __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, d
     double d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = (double)Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
+    if (c == PRESSURE) zh_fill<double>(d, (double)a.zh_dr);
     double r, u, v;
     moments_of<double>(d, (double)a.gx, (double)a.gy, (double)a.rho0, r, u, v);
     if (rho) rho[k] = r;
@@ -121,7 +123,8 @@ __global__ void k_get_f(Args<typename Fmt<S>::C> a, double* f, double* phi) {
         phi[n + k] = (double)a.phi_in[a.plane + own];
     }
     if (!f) return;
-    if (a.mask && a.mask[own] != FLUID) {
+    const int c = a.mask ? a.mask[own] : FLUID;
+    if (!collides(c)) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i * n + k] = 0.0;
         return;
@@ -129,10 +132,12 @@ __global__ void k_get_f(Args<typename Fmt<S>::C> a, double* f, double* phi) {
     long long nb[9];
     int kind[9];
     links<true>(a, x, y, nb, kind);
+    double d[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        f[i * n + k] =
-            (double)Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]) + wgt(i) * (double)a.rho0;
+    for (int i = 0; i < 9; ++i) d[i] = (double)Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
+    if (c == PRESSURE) zh_fill<double>(d, (double)a.zh_dr);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i * n + k] = d[i] + wgt(i) * (double)a.rho0;
 }
 
 // Import f_i(x, t) (FP64 [9][ny][nx]) as an even-level state; fluid nodes only.
@@ -151,7 +156,7 @@ __global__ void k_set_f(Args<typename Fmt<S>::C> a, const double* f, const doubl
         P[own] = (C)phi[k];
         P[a.plane + own] = (C)phi[n + k];
     }
-    if (a.mask && a.mask[own] != FLUID) return;
+    if (a.mask && !collides(a.mask[own])) return;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         F[(long long)i * a.plane + own] = Fmt<S>::st((C)(f[i * n + k] - wgt(i) * (double)a.rho0));
@@ -167,10 +172,12 @@ __global__ void k_phi_of_state(Args<typename Fmt<S>::C> a) {
     const S* F = static_cast<const S*>(a.f);
     C* P = const_cast<C*>(a.phi_in);
     const long long own = (long long)y * a.pitch + x;
-    if (a.mask && a.mask[own] != FLUID) return;
+    const int c = a.mask ? a.mask[own] : FLUID;
+    if (!collides(c)) return;
     C d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[(long long)i * a.plane + own]);
+    if (c == PRESSURE) zh_fill<C>(d, a.zh_dr);
     C r, u, v;
     moments_of<C>(d, a.gx, a.gy, a.rho0, r, u, v);
     P[own] = r * u * u * u;
@@ -225,7 +232,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Args<typename Fmt
          k += (long long)gridDim.x * DIAG_THREADS) {
         const int x = (int)(k % a.nx), y = (int)(k / a.nx);
         const long long own = (long long)y * a.pitch + x;
-        if (a.mask && a.mask[own] != FLUID) continue;
+        const int c = a.mask ? a.mask[own] : FLUID;
+        if (!collides(c)) continue;
         long long nb[9];
         int kind[9];
         links<true>(a, x, y, nb, kind);
@@ -236,6 +244,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Args<typename Fmt
             d[i] = (double)Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
             finite = finite && isfinite(d[i]);
         }
+        if (c == PRESSURE) zh_fill<double>(d, (double)a.zh_dr);
         if (!finite) {
             acc.v[5] += 1.0;
             continue;
@@ -248,10 +257,11 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Args<typename Fmt
         acc.v[3] += 0.5 * r * (u * u + v * v);
         acc.v[4] = fmax(acc.v[4], sqrt(u * u + v * v));
         // momentum exchange with stationary walls: links into solid nodes or
-        // across non-periodic edges carry 2 e_i f_ibar(x) (Sec. III D)
+        // across non-periodic edges carry 2 e_i f_ibar(x) (Sec. III D); the
+        // links leaving a pressure outlet across the edge are open
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const bool wall = kind[i] == K_WALL;
+            const bool wall = kind[i] == K_WALL && !(c == PRESSURE && ex(i) > 0);
             if (wall) {
                 const double fr = d[opp(i)] + wgt(opp(i)) * (double)a.rho0;
                 acc.v[6] += 2.0 * ex(i) * fr;

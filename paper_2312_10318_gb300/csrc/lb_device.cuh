@@ -34,7 +34,10 @@ __host__ __device__ constexpr double wgt(int i) {
     return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-enum : uint8_t { FLUID = 0, SOLID = 1, INLET = 2, OUTLET = 3 };
+enum : uint8_t { FLUID = 0, SOLID = 1, INLET = 2, OUTLET = 3, PRESSURE = 4 };
+
+// Classes whose nodes collide: fluid nodes and Zou-He pressure outlet nodes.
+__host__ __device__ constexpr bool collides(int c) { return c == FLUID || c == PRESSURE; }
 enum : int { K_STREAM = 0, K_WALL = 1, K_MOVING = 2 };
 enum : int { G_LAGGED = 0, G_CURRENT = 1, G_OFF = 2 };
 
@@ -78,7 +81,27 @@ template <typename C> struct Args {
     C gx, gy, rho0;
     C corr[9];            // moving-wall term 2 w_i rho_w (e_i.u_w) / c_s^2
     C phin_x, phin_y;     // Phi of moving-wall (inlet) nodes, rho_w u_w^3
+    C zh_dr;              // rho0 - outlet_rho of the Zou-He pressure outlet
 };
+
+// Zou-He constant-pressure outlet (Sec. III D) on the shifted populations
+// d_i = f_i - w_i rho0 of a node on the last column of a lattice open in x:
+// the three populations entering across the edge (e_x = -1) are rebuilt so
+// that rho = outlet_rho, rho u_y = 0 and the normal non-equilibrium parts of
+// f_(1,0) and f_(-1,0) are equal.  With j = rho_out u_x =
+// [d_0 + d_2 + d_4 + 2 (d_1 + d_5 + d_8)] + (rho0 - rho_out) (the weights of
+// f_0 + f_2 + f_4 + 2 (f_1 + f_5 + f_8) add up to 1):
+//   d_3 = d_1 - (2/3) j,  d_6 = d_8 - (d_2 - d_4)/2 - j/6,
+//   d_7 = d_5 + (d_2 - d_4)/2 - j/6.
+template <typename C>
+__device__ __forceinline__ void zh_fill(C (&d)[9], C zh_dr) {
+    const C j = (d[0] + d[2] + d[4]) + C(2) * (d[1] + d[5] + d[8]) + zh_dr;
+    const C t = C(0.5) * (d[2] - d[4]);
+    const C j6 = j * C(1.0 / 6.0);
+    d[3] = d[1] - C(4) * j6;
+    d[6] = d[8] - t - j6;
+    d[7] = d[5] + t - j6;
+}
 
 // Neighbourhood of node (x, y): wrapped coordinates and out-of-domain flags.
 struct Nbh {
@@ -263,7 +286,8 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
     using C = typename Fmt<S>::C;
     S* __restrict__ F = static_cast<S*>(a.f);
     const long long own = (long long)y * a.pitch + x;
-    if (GENERAL && a.mask && a.mask[own] != FLUID) return;
+    const int cls = (GENERAL && a.mask) ? a.mask[own] : FLUID;
+    if (GENERAL && !collides(cls)) return;
     long long nb[9];
     int kind[9];
     links<GENERAL>(a, x, y, nb, kind);
@@ -271,13 +295,16 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
     C d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
+    if (GENERAL && cls == PRESSURE) zh_fill<C>(d, a.zh_dr);
 
     C dpx = C(0), dpy = C(0);
     if (GMODE == G_LAGGED) {
         const Nbh n = neighbours(a, x, y);
         const C* Px = a.phi_in;
         const C* Py = a.phi_in + a.plane;
-        const C pxp = (GENERAL && n.oxp) ? C(0) : Px[(long long)y * a.pitch + n.xp];
+        // beyond a pressure outlet Phi continues with zero gradient
+        const C pxp = (GENERAL && n.oxp) ? (cls == PRESSURE ? Px[own] : C(0))
+                                         : Px[(long long)y * a.pitch + n.xp];
         const C pxm = (GENERAL && n.oxm) ? C(0) : Px[(long long)y * a.pitch + n.xm];
         const C pyp = (GENERAL && n.oyp) ? C(0) : Py[(long long)n.yp * a.pitch + x];
         const C pym = (GENERAL && n.oym) ? C(0) : Py[(long long)n.ym * a.pitch + x];
@@ -330,7 +357,7 @@ __global__ void k_ghosts(Args<typename Fmt<S>::C> a, const int* __restrict__ gho
     links<true>(a, zx, sy, nbz, kz);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        if (ks[i] != K_STREAM || a.mask[nbs[i]] != FLUID) continue;
+        if (ks[i] != K_STREAM || !collides(a.mask[nbs[i]])) continue;
         // where the step stored f*_i(z)
         long long src;
         if (!ODD_NEW) {  // state is even: f*_i(z) went to F[i][z + e_i] or F[ibar][z]

@@ -38,6 +38,7 @@ struct State {
     int g_mode;
     double tau1, tau2, gx, gy, rho0;
     double wall_ux, wall_uy, wall_rho;
+    double outlet_rho;    // density of Zou-He pressure outlet nodes
     int parity;           // parity of the current level
 };
 

@@ -32,6 +32,7 @@ static Args<C> make_args(const State& s, bool swap_phi = false) {
     }
     a.phin_x = (C)(s.wall_rho * s.wall_ux * s.wall_ux * s.wall_ux);
     a.phin_y = (C)(s.wall_rho * s.wall_uy * s.wall_uy * s.wall_uy);
+    a.zh_dr = (C)(s.rho0 - s.outlet_rho);
     return a;
 }
 
@@ -73,7 +74,8 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
     }
     const Args<C> a = make_args<C>(v);
     const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
-    k_step_ab<S><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
+    if (s.general) k_step_ab<S, true><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
+    else k_step_ab<S, false><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     return cudaGetLastError();
 }
 

@@ -137,6 +137,7 @@ void trtrlb_default_params(trtrlb_params* p) {
     p->magic = 0.25;
     p->rho0 = 1.0;
     p->wall_rho = 1.0;
+    p->outlet_rho = 1.0;
     p->storage = TRTRLB_F32;
     p->g_mode = TRTRLB_G_LAGGED;
 }
@@ -161,6 +162,8 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     if (!(p.rho0 > 0) || !std::isfinite(p.gx) || !std::isfinite(p.gy) ||
         !std::isfinite(p.wall_ux) || !std::isfinite(p.wall_uy) || !std::isfinite(p.wall_rho))
         return fail(err, TRTRLB_EINVAL, "rho0 must be > 0 and forces / wall state finite");
+    if (!(p.outlet_rho > 0) || !std::isfinite(p.outlet_rho))
+        return fail(err, TRTRLB_EINVAL, "outlet_rho must be finite and > 0");
 
     const int pitch = (p.nx + 63) / 64 * 64;
     const long long plane = (long long)pitch * p.ny;
@@ -169,7 +172,10 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         for (int y = 0; y < p.ny; ++y)
             for (int x = 0; x < p.nx; ++x) {
                 const uint8_t c = mask[(long long)y * p.nx + x];
-                if (c > TRTRLB_OUTLET) return fail(err, TRTRLB_EINVAL, "mask class out of range");
+                if (c > TRTRLB_PRESSURE) return fail(err, TRTRLB_EINVAL, "mask class out of range");
+                if (c == TRTRLB_PRESSURE && (p.periodic_x || x != p.nx - 1))
+                    return fail(err, TRTRLB_EINVAL,
+                                "pressure outlet nodes must lie on the last column of a lattice not periodic in x");
                 if (c != TRTRLB_OUTLET) continue;
                 int zx = x - 1;
                 if (zx < 0) {
@@ -224,6 +230,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     s.tau1 = p.tau_s; s.tau2 = tau2;
     s.gx = p.gx; s.gy = p.gy; s.rho0 = p.rho0;
     s.wall_ux = p.wall_ux; s.wall_uy = p.wall_uy; s.wall_rho = p.wall_rho;
+    s.outlet_rho = p.outlet_rho;
     s.parity = 0;
     if (ok) ok = alloc((void**)&h->part, sizeof(double) * 8 * trt::diag_blocks(s));
     if (!ok) {

@@ -167,12 +167,13 @@ def taylor_green_convergence(sizes=(32, 64, 128, 256, 512), storage="f64", g_mod
 
 def creeping_flow(re: float, d: int = 21, l_over_d: int = 50, ma: float | None = None,
                   incompressibility: float = 0.1, magic: float = 3.0 / 16.0, rlb: bool = False,
-                  storage="f64", g_mode="lagged", tol: float = 1e-9, check: int = 10000,
-                  max_steps: int = 400000, stream=None):
+                  storage="f64", g_mode="lagged", outlet: str = "pressure", tol: float = 1e-9,
+                  check: int = 10000, max_steps: int = 400000, stream=None):
     """Flow past a D x D square centred in an L x L box (L = l_over_d D, Sec. III D):
-    moving-wall inlet column at x = 0 with u_w = (u0, 0), zero-gradient outlet
-    ghost column at x = L - 1 (the paper uses a Zou-He pressure outlet), y
-    periodic, Lambda_s = 3/16 (rlb: tau_{s,2} = tau_{s,1}), starting from rest.
+    moving-wall inlet column at x = 0 with u_w = (u0, 0), outlet column at
+    x = L - 1 -- the paper's Zou-He pressure outlet at rho = 1 ("pressure") or
+    zero-gradient ghosts ("ghost") -- y periodic, Lambda_s = 3/16 (rlb:
+    tau_{s,2} = tau_{s,1}), starting from rest.
     Ma is given (the runs at Re >= 1 use Ma = 0.1) or follows T = Ma^2 / Re =
     incompressibility (the runs at Re <= 0.1).  Every `check` steps it compares u
     with u `check` steps earlier: the relative L2 change (eq_n1 with the earlier
@@ -191,7 +192,7 @@ def creeping_flow(re: float, d: int = 21, l_over_d: int = 50, ma: float | None =
     c0 = L // 2 - d // 2
     mask[c0:c0 + d, c0:c0 + d] = W.SOLID
     mask[:, 0] = W.INLET
-    mask[:, L - 1] = W.OUTLET
+    mask[:, L - 1] = {"pressure": W.PRESSURE, "ghost": W.OUTLET}[outlet]
     stream = stream or torch.cuda.Stream()
     with torch.cuda.stream(stream):
         lat = Lattice(L, L, tau1, tau_s2=tau2, periodic=(False, True), wall_u=(u0, 0.0), wall_rho=1.0,
@@ -199,7 +200,7 @@ def creeping_flow(re: float, d: int = 21, l_over_d: int = 50, ma: float | None =
         z = torch.zeros((L, L), dtype=torch.float64, device="cuda")
         lat.init(z, z)
     batch = Batch(stream).set([lat])
-    fluid = mask == W.FLUID
+    fluid = (mask == W.FLUID) | (mask == W.PRESSURE)
     prev = None
     steps, l2, du = 0, float("inf"), float("inf")
     history = []
@@ -228,7 +229,7 @@ def creeping_flow(re: float, d: int = 21, l_over_d: int = 50, ma: float | None =
             "L": L, "steps": steps, "l2_change": l2, "max_du_over_u0": du,
             "converged": l2 < tol, "diverged": diverged, "cd": cd, "cd_mu": cd * re,
             "cd_history": history[-6:], "seconds": time.perf_counter() - t0,
-            "storage": storage, "g_mode": g_mode}
+            "storage": storage, "g_mode": g_mode, "outlet": outlet}
 
 
 def sen_drag(re: float) -> float:
@@ -245,6 +246,7 @@ def main(argv):
     ap.add_argument("--re", type=float, nargs="*", default=None)
     ap.add_argument("--max-steps", type=int, default=400000)
     ap.add_argument("--rlb", action="store_true", help="creeping flow with tau_{s,2} = tau_{s,1}")
+    ap.add_argument("--outlet", choices=["pressure", "ghost"], default="pressure")
     a = ap.parse_args(argv[1:])
     kw = {k: v for k, v in (("storage", a.storage), ("g_mode", a.g_mode)) if v is not None}
     log = lambda m: print(m, file=sys.stderr, flush=True)
@@ -256,14 +258,14 @@ def main(argv):
     elif a.experiment == "sen":
         out = []
         for re in (a.re or (2.0, 5.0, 10.0, 20.0)):
-            r = creeping_flow(re, ma=0.1, max_steps=a.max_steps, **kw)
+            r = creeping_flow(re, ma=0.1, max_steps=a.max_steps, outlet=a.outlet, **kw)
             r["sen"] = sen_drag(re)
             out.append(r)
             log(json.dumps(r, default=str))
     else:
         out = []
         for re in (a.re or (1e-1, 1e-2, 1e-3)):
-            r = creeping_flow(re, rlb=a.rlb, max_steps=a.max_steps, **kw)
+            r = creeping_flow(re, rlb=a.rlb, max_steps=a.max_steps, outlet=a.outlet, **kw)
             out.append(r)
             log(json.dumps(r, default=str))
     print(json.dumps({"experiment": a.experiment, "seconds": time.perf_counter() - t0, "result": out},

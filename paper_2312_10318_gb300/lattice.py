@@ -55,14 +55,15 @@ class Lattice:
     periodic: (x, y); a non-periodic direction has stationary half-way
     bounce-back walls just outside the domain.  g: body acceleration (F = rho
     g).  mask: [ny, nx] uint8 of node classes (0 fluid, 1 solid, 2 inlet, 3
-    outlet ghost) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16' | 'f64dw' (FP64
+    outlet ghost, 4 Zou-He pressure outlet at density outlet_rho on the last
+    column) or None.  storage: 'f64' | 'f32' | 'f16' | 'bf16' | 'f64dw' (FP64
     storage, double-word FP32 arithmetic).
     g_mode: 'lagged' | 'current' | 'off'.  stream: a torch.cuda.Stream or raw handle
     (default: the current torch stream).
     """
 
     def __init__(self, nx, ny, tau_s, *, tau_s2=None, magic=None, periodic=(True, True),
-                 g=(0.0, 0.0), rho0=1.0, wall_u=(0.0, 0.0), wall_rho=1.0, storage="f32",
+                 g=(0.0, 0.0), rho0=1.0, wall_u=(0.0, 0.0), wall_rho=1.0, outlet_rho=1.0, storage="f32",
                  g_mode="lagged", mask=None, stream=None):
         lib = _lib.load()
         p = _lib.Params()
@@ -76,6 +77,7 @@ class Lattice:
         p.rho0 = float(rho0)
         p.wall_ux, p.wall_uy = float(wall_u[0]), float(wall_u[1])
         p.wall_rho = float(wall_rho)
+        p.outlet_rho = float(outlet_rho)
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.g_mode = G_MODE[g_mode] if isinstance(g_mode, str) else int(g_mode)
         self.nx, self.ny, self.storage = p.nx, p.ny, storage

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import params as P
 
-FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+FLUID, SOLID, INLET, OUTLET, PRESSURE = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -106,9 +106,10 @@ def poiseuille(ny: int, tau_s: float, magic: float, nx: int = 8, u_c: float = 0.
 
 def creeping_flow(nx: int = 4096, ny: int = 2048, side: int = 64, center_x: Optional[int] = None,
                   re: float = 1.0, incompressibility: float = 0.1, magic: float = 3.0 / 16.0,
-                  steps: int = 1000) -> Problem:
+                  steps: int = 1000, outlet: int = OUTLET) -> Problem:
     """Flow past a square cylinder (Sec. III D): moving-wall inlet column x = 0
-    with u_w = (u0, 0), zero-gradient outlet ghost column x = nx - 1, y periodic,
+    with u_w = (u0, 0), outlet column x = nx - 1 (zero-gradient ghosts, or the
+    paper's Zou-He pressure outlet at rho = 1 with outlet=PRESSURE), y periodic,
     a side x side solid square centred at (center_x, ny/2).  Starts from rest."""
     ma, u0, tau_s = P.creeping_flow(re, incompressibility, side)
     cx = nx // 4 if center_x is None else center_x
@@ -116,7 +117,7 @@ def creeping_flow(nx: int = 4096, ny: int = 2048, side: int = 64, center_x: Opti
     x0, y0 = cx - side // 2, ny // 2 - side // 2
     mask[y0:y0 + side, x0:x0 + side] = SOLID
     mask[:, 0] = INLET
-    mask[:, nx - 1] = OUTLET
+    mask[:, nx - 1] = outlet
     ux = np.zeros((ny, nx))
     uy = np.zeros((ny, nx))
     return Problem("creeping_flow", nx, ny, tau_s, P.tau2_from_magic(tau_s, magic), ux, uy, None,
@@ -141,14 +142,15 @@ def random_fields(nx: int, ny: int, seed: int = 0, u_amp: float = 0.05, rho_amp:
 
 
 def random_mask(nx: int, ny: int, seed: int = 0, solid_frac: float = 0.1,
-                inlet_outlet: bool = False) -> np.ndarray:
-    """Seeded random obstacle mask; optional inlet column x = 0 and outlet x = nx - 1
-    (the column next to the outlet is kept fluid)."""
+                inlet_outlet: bool = False, outlet: int = OUTLET) -> np.ndarray:
+    """Seeded random obstacle mask; optional inlet column x = 0 and outlet column
+    x = nx - 1 of class `outlet` (zero-gradient ghosts or Zou-He pressure nodes;
+    the column next to the outlet is kept fluid)."""
     rng = np.random.default_rng(seed)
     m = np.where(rng.uniform(size=(ny, nx)) < solid_frac, SOLID, FLUID).astype(np.uint8)
     if inlet_outlet:
         m[:, 0] = INLET
         m[:, nx - 2:] = FLUID
         m[:, nx - 3] = np.where(m[:, nx - 3] == SOLID, FLUID, m[:, nx - 3])
-        m[:, nx - 1] = OUTLET
+        m[:, nx - 1] = outlet
     return m

@@ -94,3 +94,33 @@ def test_lag_of_phi_is_a_higher_order_effect(gpu_lib):
     err = O.l2(sol["current"], exact)
     print(f"TG64 1000 steps: |lagged - current| = {lag:.3e}, |current - analytic| = {err:.3e}")
     assert lag < 1e-2 * err
+
+
+@pytest.mark.parametrize("storage,bound", [("f32", 3e-5), ("f16", 1.5e-2), ("bf16", 2e-1)])
+@pytest.mark.parametrize("n", [64, 67])
+def test_current_phi_reduced_precision_taylor_green(gpu_lib, storage, bound, n):
+    """The two-buffer kernel in FP32 / FP16 / BF16 storage (periodic path, full
+    and partial tiles) against the FP64 oracle's CURRENT mode: the velocity
+    bounds of the in-place kernels' Taylor-Green test."""
+    pr = W.taylor_green(n, 0.04, 100.0, magic=0.25)
+    G = gpu_lattice(pr, storage, "current").init(pr.ux, pr.uy, pr.rho)
+    R = oracle_lattice(pr, "current").init(pr.ux, pr.uy, pr.rho)
+    G.step(1000)
+    R.step(1000)
+    e = field_errors(G, R)
+    assert max(e["ux"], e["uy"]) < bound, e
+
+
+@pytest.mark.parametrize("nx,ny", [(1024, 1024), (4096, 2048)])
+def test_current_phi_full_size_fp32(gpu_lib, nx, ny):
+    """Benchmark-size lattices (FP32, periodic) against the oracle for 2 steps."""
+    pr = W.double_shear_layer(nx, re=1e4)
+    if ny != nx:
+        pr = W.Problem("dsl", nx, ny, pr.tau_s, pr.tau_s2, np.ascontiguousarray(pr.ux[:ny]),
+                       np.ascontiguousarray(pr.uy[:ny]), None)
+    G = gpu_lattice(pr, "f32", "current").init(pr.ux, pr.uy)
+    R = oracle_lattice(pr, "current").init(pr.ux, pr.uy)
+    G.step(2)
+    R.step(2)
+    e = field_errors(G, R)
+    assert max(e["ux"], e["uy"]) < 1e-5, e

@@ -1,0 +1,78 @@
+"""The paper's experiments through the GPU library, against the values the paper
+prints: the double shear layer stability limits (Sec. III A), second-order grid
+convergence of the Taylor-Green vortex (Sec. III B) and the square-cylinder drag
+(Sec. III D, Sen's law and Table 1)."""
+import math
+import os
+
+import pytest
+
+from paper_2312_10318_gb300 import experiments as E
+
+pytestmark = pytest.mark.gpu
+
+
+def test_taylor_green_second_order_convergence(gpu_lib):
+    r = E.taylor_green_convergence(sizes=(32, 64, 128))
+    assert all(abs(o - 2.0) < 0.05 for o in r["orders"]), r
+    assert r["l2"][1] < 1e-3, r
+
+
+def test_stability_peak_at_re_5e3_is_the_papers(gpu_lib):
+    # Sec. III A: the largest Ma_c of TRT-RLB at Re = 5e3 is 0.62 (to the 0.01
+    # grid), reached around 1/tau_s2 = 0.9 ... 1.1; RLB (tau_s2 = tau_s1) 0.49
+    r = E.stability_map(re_list=(5e3,), inv_tau2=[0.9, 1.1], ma_max=0.66, rlb=False)
+    best = max(r["trt_rlb"][5e3].values())
+    assert abs(best - 0.62) <= 0.01 + 1e-9, r
+    r = E.stability_map(re_list=(5e3,), inv_tau2=[], ma_max=0.52, rlb=True)
+    assert abs(r["rlb"][5e3] - 0.49) <= 0.02 + 1e-9, r
+
+
+def test_stability_at_re_1e7_beats_rlb(gpu_lib):
+    # Sec. III A: at high Re the best Ma_c of TRT-RLB stays above 0.51 (near
+    # 1/tau_s2 = 1.6) while RLB only reaches about 0.12 ... 0.15
+    r = E.stability_map(re_list=(1e7,), inv_tau2=[1.5, 1.6, 1.7], ma_max=0.60, rlb=False)
+    assert max(r["trt_rlb"][1e7].values()) > 0.51, r
+    r = E.stability_map(re_list=(1e7,), inv_tau2=[], ma_max=0.20, rlb=True)
+    assert 0.11 <= r["rlb"][1e7] <= 0.15 + 1e-9, r
+
+
+@pytest.mark.parametrize("re,tol", [(2.0, 0.04), (20.0, 0.02)])
+def test_square_cylinder_drag_against_sen_law(gpu_lib, re, tol):
+    # Sec. III D: Ma = 0.1, D = 21, L = 50 D, Zou-He outlet; Sen's empirical
+    # law for an unbounded cylinder (this box is periodic in y, blockage 1/50)
+    r = E.creeping_flow(re, ma=0.1, storage="f64dw", max_steps=150000)
+    assert not r["diverged"], r
+    (_, c1), (_, c2) = r["cd_history"][-2:]
+    assert abs(c2 / c1 - 1.0) < 1e-5, r            # C_d settled
+    assert abs(r["cd"] / E.sen_drag(re) - 1.0) < tol, r
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_creeping_flow.txt")
+
+
+def _table1():
+    """{Re: (C_d,mu TRT-RLB, C_d,mu RLB)} as Table 1 prints them."""
+    out = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            v = [float(t) for t in line.split()]
+            out[v[0]] = (v[4], v[5])
+    return out
+
+
+@pytest.mark.parametrize("re,rlb", [(0.1, False), (1e-3, False), (0.1, True)])
+def test_creeping_flow_viscous_drag_table1(gpu_lib, re, rlb):
+    # Table 1 (T = 0.1, D = 21, L = 50 D, Zou-He outlet): C_d,mu = C_d Re of
+    # TRT-RLB and of RLB (tau_s2 = tau_s1), printed to 4 digits
+    paper = _table1()[re][1 if rlb else 0]
+    r = E.creeping_flow(re, rlb=rlb, storage="f64dw", max_steps=200000)
+    assert not r["diverged"], r
+    assert abs(r["cd_mu"] / paper - 1.0) < 1e-3, r
+
+
+def test_creeping_flow_rlb_diverges_at_re_1e_3(gpu_lib):
+    # Table 1: RLB diverges at Re <= 1e-3 (tau_s1 = 364) where TRT-RLB converges
+    assert math.isnan(_table1()[1e-3][1])
+    r = E.creeping_flow(1e-3, rlb=True, storage="f64dw", max_steps=100000)
+    assert r["diverged"] or not math.isfinite(r["cd"]) or r["max_du_over_u0"] > 1.0, r
