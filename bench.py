@@ -191,6 +191,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself
+    without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest (weak scaling)."""
+    return units_per_rank * world / seconds
+
+
 def cpu_baseline(problems, seconds: float = 12.0):
     """The FP64 CPU oracle on a bounded sample of the workload: as many time steps
     of the first lattice as fit in about `seconds`."""
@@ -440,12 +457,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in events]
     clk = clocks.stop() if clocks else None
     local_ms = sum(step_ms)
-    total_ms = local_ms
-    if dist is not None:
-        t = torch.tensor([local_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = nodes * args.steps * world / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(local_ms, dist)
+    value = whole_job_rate(nodes * args.steps, world, total_ms / 1e3) / 1e6
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
     # the two-buffer (current-Phi) kernel runs one launch per lattice in a batch
@@ -473,12 +486,8 @@ def main():
             lat.moments(*out)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = statistics.median(e2e_times) if e2e_times else float("nan")
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = nodes * args.e2e_steps * world / e2e_t / 1e6
+    e2e_t = max_over_ranks(statistics.median(e2e_times) if e2e_times else float("nan"), dist)
+    e2e_value = whole_job_rate(nodes * args.e2e_steps, world, e2e_t) / 1e6
     field_bytes = 3 * 8 * nodes
 
     if rank == 0:

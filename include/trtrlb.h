@@ -84,6 +84,10 @@ extern "C" {
                            the edge is the node's own.  Every read of the
                            state (step, moments, populations, diagnostics)
                            sees the rebuilt values.                          */
+#define TRTRLB_HALO 5   /* halo node of a sub-lattice (trtrlb_slabs_*): stands
+                           for a fluid node another sub-lattice updates; it
+                           does not collide, links into it stream, and its
+                           populations and Phi are written by the exchange  */
 
 /* Problem statement (Sec. II B, eq2; eq_mu; eq_a2; eq_a29). */
 typedef struct {
@@ -214,6 +218,40 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w);
 /* The kernel in use: *vector = 1 for the vector kernel; *tile_w as above.
  * Either pointer may be NULL. */
 int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w);
+
+/* ---- slab decomposition -----------------------------------------------------
+ * One lattice split into nslabs sub-lattices of consecutive rows (y), the
+ * single-device form of a multi-GPU domain split (the paper has none; its
+ * scheme is node-local apart from streaming and d Phi, so a split needs only a
+ * one-row halo).  Slab k owns rows [row0_k, row0_k + rows_k) (rows as even as
+ * possible, the first ny % nslabs slabs one more) and is a lattice handle of
+ * its own, with a TRTRLB_HALO row on each side that faces another slab (both
+ * sides when the lattice is periodic in y).  Every step exchanges rows with
+ * device copies on the slabs' stream: before it, the previous level's
+ * Phi_yyy of the boundary rows (LAGGED); around a step from an odd level of
+ * the in-place pattern, the y-moving populations of the boundary rows (in
+ * before, out after).  Results equal the undivided lattice's bit for bit.
+ * G_CURRENT and masks with outlet ghosts (or halo nodes) give ENOTSUP; host or
+ * device pointers are accepted where fields are passed (global [ny][nx] /
+ * [9][ny][nx] layouts); calls synchronise except step. */
+typedef struct trtrlb_slabs* trtrlb_slabs_t;
+int trtrlb_slabs_create(const trtrlb_params* p, const uint8_t* mask, int32_t nslabs, void* stream,
+                        trtrlb_slabs_t* out);
+int trtrlb_slabs_destroy(trtrlb_slabs_t s);
+int trtrlb_slabs_init(trtrlb_slabs_t s, const double* rho, const double* ux, const double* uy);
+int trtrlb_slabs_step(trtrlb_slabs_t s, int64_t nsteps);
+int trtrlb_slabs_get_f(trtrlb_slabs_t s, double* f);
+int trtrlb_slabs_moments(trtrlb_slabs_t s, double* rho, double* ux, double* uy);
+/* Sums (mass, momenta, energy, non-finite count, wall force) and the maximum
+ * speed over the slabs' owned nodes; out: 8 doubles, host or device. */
+int trtrlb_slabs_diagnostics(trtrlb_slabs_t s, double* out);
+/* Number of slabs; slab k's handle, first owned global row, owned rows and
+ * whether it has a halo row below (its owned rows then start at local row 1).
+ * The handles stay owned by s. */
+int32_t trtrlb_slabs_count(trtrlb_slabs_t s);
+int trtrlb_slabs_slab(trtrlb_slabs_t s, int32_t k, trtrlb_t* h, int32_t* row0, int32_t* rows,
+                      int32_t* halo_below);
+const char* trtrlb_slabs_last_error(trtrlb_slabs_t s);
 
 /* ---- batches ---------------------------------------------------------------
  * A batch advances several lattices together: per time step one kernel launch

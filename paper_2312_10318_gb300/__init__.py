@@ -8,13 +8,13 @@ library; constructing a Lattice does, and fails loudly if it is not built.
 """
 from __future__ import annotations
 
-__all__ = ["Lattice", "params", "workloads"]
+__all__ = ["Lattice", "Slabs", "params", "workloads"]
 
 
 def __getattr__(name):
-    if name == "Lattice":
-        from .lattice import Lattice
-        return Lattice
+    if name in ("Lattice", "Slabs"):
+        from . import lattice
+        return getattr(lattice, name)
     if name in ("params", "workloads"):
         import importlib
         return importlib.import_module(f".{name}", __name__)

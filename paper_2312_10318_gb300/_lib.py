@@ -57,6 +57,17 @@ SIGNATURES = {
     "trtrlb_batch_step": (C.c_int, [_vp, _i64]),
     "trtrlb_batch_destroy": (C.c_int, [_vp]),
     "trtrlb_batch_last_error": (C.c_char_p, [_vp]),
+    "trtrlb_slabs_create": (C.c_int, [C.POINTER(Params), _vp, C.c_int32, _vp, C.POINTER(_vp)]),
+    "trtrlb_slabs_destroy": (C.c_int, [_vp]),
+    "trtrlb_slabs_init": (C.c_int, [_vp, _dp, _dp, _dp]),
+    "trtrlb_slabs_step": (C.c_int, [_vp, _i64]),
+    "trtrlb_slabs_get_f": (C.c_int, [_vp, _dp]),
+    "trtrlb_slabs_moments": (C.c_int, [_vp, _dp, _dp, _dp]),
+    "trtrlb_slabs_diagnostics": (C.c_int, [_vp, _dp]),
+    "trtrlb_slabs_count": (C.c_int32, [_vp]),
+    "trtrlb_slabs_slab": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "trtrlb_slabs_last_error": (C.c_char_p, [_vp]),
     "trtrlb_strerror": (C.c_char_p, [C.c_int]),
     "trtrlb_last_error": (C.c_char_p, [_vp]),
 }

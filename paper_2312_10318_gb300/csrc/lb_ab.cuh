@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(AB_TX * AB_TY, 4) k_step_ab(Args<typename Fmt<
     for (int i = 0; i < 9; ++i) {
         int txn = x + ex(i), tyn = y + ey(i);
         const int c = i == 0 ? FLUID : ab_class(a, txn, tyn);
-        if (collides(c)) {
+        if (collides(c) || c == HALO) {
             dst[(long long)i * a.plane + (long long)tyn * a.pitch + txn] = Fmt<S>::st(o[i]);
         } else if (c == SOLID || c == AB_OUT) {
             // (across the edge of a pressure outlet this fills a population

@@ -172,7 +172,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         for (int y = 0; y < p.ny; ++y)
             for (int x = 0; x < p.nx; ++x) {
                 const uint8_t c = mask[(long long)y * p.nx + x];
-                if (c > TRTRLB_PRESSURE) return fail(err, TRTRLB_EINVAL, "mask class out of range");
+                if (c > TRTRLB_HALO) return fail(err, TRTRLB_EINVAL, "mask class out of range");
                 if (c == TRTRLB_PRESSURE && (p.periodic_x || x != p.nx - 1))
                     return fail(err, TRTRLB_EINVAL,
                                 "pressure outlet nodes must lie on the last column of a lattice not periodic in x");

@@ -237,3 +237,106 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Slabs:
+    """One lattice split into `nslabs` sub-lattices of consecutive rows with a
+    one-row halo exchange between steps (the single-device form of a domain
+    split; results equal the undivided Lattice bit for bit).  Arguments as for
+    Lattice; G mode 'lagged' or 'off'; no outlet ghosts in the mask."""
+
+    def __init__(self, nx, ny, tau_s, nslabs, *, tau_s2=None, magic=None, periodic=(True, True),
+                 g=(0.0, 0.0), rho0=1.0, wall_u=(0.0, 0.0), wall_rho=1.0, outlet_rho=1.0,
+                 storage="f32", g_mode="lagged", mask=None, stream=None):
+        lib = _lib.load()
+        p = _lib.Params()
+        lib.trtrlb_default_params(C.byref(p))
+        p.nx, p.ny = int(nx), int(ny)
+        p.periodic_x, p.periodic_y = int(bool(periodic[0])), int(bool(periodic[1]))
+        p.tau_s = float(tau_s)
+        p.tau_s2 = math.nan if tau_s2 is None else float(tau_s2)
+        p.magic = math.nan if magic is None else float(magic)
+        p.gx, p.gy = float(g[0]), float(g[1])
+        p.rho0 = float(rho0)
+        p.wall_ux, p.wall_uy = float(wall_u[0]), float(wall_u[1])
+        p.wall_rho = float(wall_rho)
+        p.outlet_rho = float(outlet_rho)
+        p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        p.g_mode = G_MODE[g_mode] if isinstance(g_mode, str) else int(g_mode)
+        self.nx, self.ny, self.storage = p.nx, p.ny, storage
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            if m.shape != (self.ny, self.nx):
+                raise ValueError("mask must be [ny, nx]")
+        self._mask = m
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        rc = lib.trtrlb_slabs_create(C.byref(p), None if m is None else m.ctypes.data, int(nslabs),
+                                     C.c_void_p(stream), C.byref(h))
+        if rc != _lib.OK:
+            msg = lib.trtrlb_last_error(None)
+            raise _lib.TrtrlbError(rc, f"{lib.trtrlb_strerror(rc).decode()}: {msg.decode() if msg else ''}")
+        self._h, self._lib = h, lib
+
+    def _chk(self, rc):
+        if rc != _lib.OK:
+            msg = self._lib.trtrlb_slabs_last_error(self._h)
+            raise _lib.TrtrlbError(rc, f"{self._lib.trtrlb_strerror(rc).decode()}: {msg.decode() if msg else ''}")
+        return rc
+
+    @property
+    def count(self) -> int:
+        return int(self._lib.trtrlb_slabs_count(self._h))
+
+    def rows(self):
+        """[(first global row, rows)] of every slab."""
+        out = []
+        for k in range(self.count):
+            r0, n = C.c_int32(), C.c_int32()
+            self._chk(self._lib.trtrlb_slabs_slab(self._h, k, None, C.byref(r0), C.byref(n), None))
+            out.append((r0.value, n.value))
+        return out
+
+    def init(self, ux, uy, rho=None):
+        sh = (self.ny, self.nx)
+        ux, uy, rho = _as_f64(ux, sh), _as_f64(uy, sh), _as_f64(rho, sh)
+        self._chk(self._lib.trtrlb_slabs_init(self._h, _ptr(rho, sh), _ptr(ux, sh), _ptr(uy, sh)))
+        return self
+
+    def step(self, n: int = 1):
+        self._chk(self._lib.trtrlb_slabs_step(self._h, int(n)))
+        return self
+
+    def get_f(self):
+        f = np.empty((9, self.ny, self.nx))
+        self._chk(self._lib.trtrlb_slabs_get_f(self._h, _ptr(f)))
+        return f
+
+    def moments(self):
+        sh = (self.ny, self.nx)
+        rho, ux, uy = (np.empty(sh) for _ in range(3))
+        self._chk(self._lib.trtrlb_slabs_moments(self._h, _ptr(rho), _ptr(ux), _ptr(uy)))
+        return rho, ux, uy
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(8)
+        self._chk(self._lib.trtrlb_slabs_diagnostics(self._h, _ptr(out)))
+        keys = ("mass", "momentum_x", "momentum_y", "kinetic_energy", "max_u", "nonfinite",
+                "wall_force_x", "wall_force_y")
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.trtrlb_slabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
