@@ -204,7 +204,8 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
 /* Kernel shape of a lattice's step (the autotuner's knobs; results do not
  * depend on them).  variant: TRTRLB_KERNEL_AUTO (the vector kernel where it
  * applies for FP32/FP16/BF16, the scalar one for FP64 and F64_DW),
- * TRTRLB_KERNEL_SCALAR (one node per thread), TRTRLB_KERNEL_VECTOR
+ * TRTRLB_KERNEL_SCALAR (one node per thread; for G_CURRENT the plain
+ * two-buffer kernel instead of the TMA-fed one), TRTRLB_KERNEL_VECTOR
  * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
  * lattice is periodic in both directions, has no mask and nx is a multiple
  * of that width).
@@ -214,6 +215,15 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
 #define TRTRLB_KERNEL_SCALAR 1
 #define TRTRLB_KERNEL_VECTOR 2
 int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w);
+
+/* Bounded waits.  The TMA-fed G_CURRENT kernel (FP32, periodic, no mask)
+ * waits on an mbarrier for each tile copy; after `polls` unsuccessful polls
+ * (default 4,194,304: far beyond a copy's microseconds) it records the failure,
+ * drains its copies in flight and returns, and the next trtrlb_moments /
+ * trtrlb_get_f / trtrlb_diagnostics with host outputs reports TRTRLB_ETIMEOUT
+ * (the state of that step is then undefined).  polls = 0 makes every such wait
+ * give up at once, to exercise that path. */
+int trtrlb_set_wait_limit(trtrlb_t h, int64_t polls);
 
 /* The kernel in use: *vector = 1 for the vector kernel; *tile_w as above.
  * Either pointer may be NULL. */

@@ -22,6 +22,9 @@ struct trtrlb_lattice {
     int64_t bytes;
     int tile_w;          // scalar-kernel tile width in the batched path (32 .. 256 nodes)
     int variant;         // TRTRLB_KERNEL_AUTO / SCALAR / VECTOR
+    void* tmaps;         // two CUtensorMap (host) of the FP32 periodic G_CURRENT kernel, or null
+    int* kerr;           // device flag set when a kernel's bounded wait ran out, or null
+    int tma_grid;        // persistent grid of the TMA kernel on this device (0: none)
     char err[256];
 };
 

@@ -21,6 +21,13 @@ constexpr int VEC16_NODES = 4;
 inline int vec_width(int storage_bytes) { return storage_bytes == 2 ? VEC16_NODES : 16 / storage_bytes; }
 
 // Format-independent description of a lattice's device state.
+// Box of the TMA-fed two-buffer kernel (lb_ab_tma.cuh): x0-4 .. x0+35 by
+// y0-1 .. y0+8 around a 32 x 8 tile, all 9 population planes.
+constexpr int TMA_BX = 40, TMA_BY = 10, TMA_XOFF = 4;
+// Polls of an mbarrier before a kernel's wait gives up (microseconds suffice
+// for a tile copy; the limit only bounds a wait that would never end).
+constexpr long long kDefaultWaitLimit = 1ll << 22;
+
 struct State {
     void* f;              // populations, S[9][ny][pitch]
     void* f2;             // second buffer of the two-buffer G_CURRENT kernel (else null)
@@ -40,6 +47,13 @@ struct State {
     double wall_ux, wall_uy, wall_rho;
     double outlet_rho;    // density of Zou-He pressure outlet nodes
     int parity;           // parity of the current level
+    // FP32 periodic G_CURRENT lattices: TMA descriptors (CUtensorMap, host
+    // memory) of the population buffers, tma_map[k] describing tma_buf[k]
+    const void* tma_buf[2];
+    const void* tma_map[2];
+    int tma_grid;         // persistent grid of the TMA kernel (0: not used)
+    int* kerr;            // device flag: a kernel's bounded wait ran out
+    long long wait_limit; // polls before a kernel's wait gives up
 };
 
 template <typename S> struct Ops {
@@ -66,6 +80,9 @@ template <typename S> struct Ops {
     // Two-buffer G_CURRENT step q of a sequence starting from s.f (the buffers
     // alternate with q); the caller swaps s.f / s.f2 after an odd count.
     static cudaError_t step_ab(const State& s, int q, cudaStream_t st);
+    // Persistent grid (resident CTAs per SM x SMs) of the TMA-fed two-buffer
+    // kernel on the current device; 0 for formats that do not have it.
+    static int tma_grid();
 };
 
 int diag_blocks(const State& s);

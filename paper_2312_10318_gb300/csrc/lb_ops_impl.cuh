@@ -1,6 +1,9 @@
 // Definitions of Ops<S> (lb_ops.cuh); included once per storage format.
 #pragma once
+#include <type_traits>
+
 #include "lb_ab.cuh"
+#include "lb_ab_tma.cuh"
 #include "lb_aux.cuh"
 #include "lb_batch.cuh"
 #include "lb_ops.cuh"
@@ -74,9 +77,35 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
     }
     const Args<C> a = make_args<C>(v);
     const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
+    if constexpr (std::is_same<S, float>::value) {
+        if (!s.general && s.tma_grid > 0 && s.kerr) {
+            const int k = v.f == s.tma_buf[0] ? 0 : 1;
+            const CUtensorMap* map = static_cast<const CUtensorMap*>(s.tma_map[k]);
+            const int ntiles = (int)(g.x * g.y);
+            const int grid = ntiles < s.tma_grid ? ntiles : s.tma_grid;
+            k_step_ab_tma<S><<<grid, AB_TX * AB_TY, 0, st>>>(*map, a, static_cast<S*>(v.f2), (int)g.x,
+                                                             ntiles, s.kerr, s.wait_limit);
+            return cudaGetLastError();
+        }
+    }
     if (s.general) k_step_ab<S, true><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     else k_step_ab<S, false><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     return cudaGetLastError();
+}
+
+template <typename S>
+int Ops<S>::tma_grid() {
+    if constexpr (std::is_same<S, float>::value) {
+        int dev = 0, sms = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_ab_tma<S>, AB_TX * AB_TY, 0) !=
+                cudaSuccess)
+            return 0;
+        return occ * sms;
+    } else {
+        return 0;
+    }
 }
 
 template <typename S>

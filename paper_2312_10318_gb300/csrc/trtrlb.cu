@@ -1,6 +1,7 @@
 // C ABI of the D2Q9 TRT-RLB library (declared in include/trtrlb.h).
 // Owns the device memory of each lattice, validates the problem statement and
 // dispatches to the per-format launchers (lb_ops.cuh).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -76,7 +77,20 @@ void release(trtrlb_lattice* h) {
     if (h->stage) cudaFree(h->stage);
     if (h->part) cudaFree(h->part);
     if (h->dout) cudaFree(h->dout);
+    if (h->kerr) cudaFree(h->kerr);
+    delete[] static_cast<CUtensorMap*>(h->tmaps);
     delete h;
+}
+
+// TRTRLB_ETIMEOUT if a kernel of the handle reported a bounded wait that ran
+// out (the flag is cleared); call after the handle's stream is synchronised.
+int check_kerr(trtrlb_lattice* h) {
+    if (!h->kerr) return TRTRLB_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, h->kerr, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return TRTRLB_ECUDA;
+    if (!v) return TRTRLB_OK;
+    cudaMemset(h->kerr, 0, sizeof v);
+    return fail(h->err, TRTRLB_ETIMEOUT, "a step kernel's wait for its tile copy ran out");
 }
 
 // The vector kernel needs a periodic lattice without mask and nx divisible
@@ -103,6 +117,34 @@ cudaError_t ensure_stage(trtrlb_lattice* h) {
     if (e == cudaSuccess) h->bytes += (int64_t)bytes;
     else h->stage = nullptr;
     return e;
+}
+
+// TMA descriptor of one FP32 population buffer for k_step_ab_tma: a 3-D tensor
+// (x: nx, y: ny rows of `pitch` floats, plane: 9 planes of ny * pitch floats)
+// read in boxes of 40 x 10 x 9 (the 32 x 8 tile, its one-node halo and the
+// columns that keep the box origin 16-byte aligned); outside the lattice the
+// box is filled with zeros.
+cudaError_t encode_tma(void* base, int nx, int ny, int pitch, CUtensorMap* out) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                                               cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr) return cudaErrorNotSupported;
+        fn = reinterpret_cast<Encode>(ptr);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)trt::TMA_BX, (cuuint32_t)trt::TMA_BY, 9};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Resolves tau_s2 from tau_s2 / magic (eq_a29).  Returns 0 or an error code.
@@ -232,6 +274,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     s.wall_ux = p.wall_ux; s.wall_uy = p.wall_uy; s.wall_rho = p.wall_rho;
     s.outlet_rho = p.outlet_rho;
     s.parity = 0;
+    s.wait_limit = trt::kDefaultWaitLimit;
     if (ok) ok = alloc((void**)&h->part, sizeof(double) * 8 * trt::diag_blocks(s));
     if (!ok) {
         const int rc = e == cudaErrorMemoryAllocation ? TRTRLB_ENOMEM : TRTRLB_ECUDA;
@@ -268,6 +311,29 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     s.tile_w = h->tile_w;
     h->variant = TRTRLB_KERNEL_AUTO;
     s.vec = auto_vector(h);
+    if (p.g_mode == TRTRLB_G_CURRENT && p.storage == TRTRLB_F32 && !s.general) {
+        // the TMA-fed two-buffer kernel; without a descriptor the plain one runs
+        CUtensorMap* maps = new (std::nothrow) CUtensorMap[2];
+        e = maps ? cudaMalloc((void**)&h->kerr, sizeof(int)) : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemset(h->kerr, 0, sizeof(int));
+        if (e == cudaSuccess) e = encode_tma(h->f, p.nx, p.ny, pitch, &maps[0]);
+        if (e == cudaSuccess) e = encode_tma(h->f2, p.nx, p.ny, pitch, &maps[1]);
+        if (e == cudaSuccess) {
+            h->tmaps = maps;
+            s.tma_buf[0] = h->f;
+            s.tma_buf[1] = h->f2;
+            s.tma_map[0] = &maps[0];
+            s.tma_map[1] = &maps[1];
+            s.kerr = h->kerr;
+            h->tma_grid = trt::Ops<float>::tma_grid();
+            s.tma_grid = h->tma_grid;
+        } else {
+            delete[] maps;
+            if (h->kerr) cudaFree(h->kerr);
+            h->kerr = nullptr;
+            cudaGetLastError();
+        }
+    }
     *out = h;
     return TRTRLB_OK;
 }
@@ -345,7 +411,7 @@ int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy) {
             e = cudaMemcpyAsync(dst[q], dev[q], nb, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && host) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h->err, e, "moments");
-    return TRTRLB_OK;
+    return host ? check_kerr(h) : TRTRLB_OK;
 }
 
 int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
@@ -370,7 +436,7 @@ int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
     }
     if (e == cudaSuccess && host) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h->err, e, "get_f");
-    return TRTRLB_OK;
+    return host ? check_kerr(h) : TRTRLB_OK;
 }
 
 int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi) {
@@ -409,7 +475,7 @@ int trtrlb_diagnostics(trtrlb_t h, double* out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h->err, e, "diagnostics");
-    return TRTRLB_OK;
+    return dev ? TRTRLB_OK : check_kerr(h);
 }
 
 int64_t trtrlb_device_bytes(trtrlb_t h) { return h ? h->bytes : -1; }
@@ -434,7 +500,17 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
     }
     h->variant = variant;
     h->s.vec = vec;
+    // G_CURRENT: AUTO runs the TMA-fed kernel where it exists, SCALAR the plain one
+    h->s.tma_grid = variant == TRTRLB_KERNEL_SCALAR ? 0 : h->tma_grid;
     if (tile_w) h->tile_w = h->s.tile_w = tile_w;
+    return TRTRLB_OK;
+}
+
+int trtrlb_set_wait_limit(trtrlb_t h, int64_t polls) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (polls < 0) return fail(h->err, TRTRLB_EINVAL, "polls must be >= 0");
+    h->s.wait_limit = polls;
     return TRTRLB_OK;
 }
 

@@ -148,6 +148,11 @@ class Lattice:
         self._chk(self._lib.trtrlb_set_kernel(self._h, v, int(tile_w)))
         return self
 
+    def set_wait_limit(self, polls: int):
+        """Polls before a kernel's bounded wait gives up (0: at once)."""
+        self._chk(self._lib.trtrlb_set_wait_limit(self._h, int(polls)))
+        return self
+
     def kernel(self):
         """(vector kernel in use, scalar tile width)."""
         vec, tw = C.c_int32(), C.c_int32()

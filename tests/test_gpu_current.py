@@ -124,3 +124,40 @@ def test_current_phi_full_size_fp32(gpu_lib, nx, ny):
     R.step(2)
     e = field_errors(G, R)
     assert max(e["ux"], e["uy"]) < 1e-5, e
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (7, 5), (33, 17), (64, 64), (130, 9), (1, 40), (257, 31),
+                                   (1024, 1024)])
+def test_tma_kernel_matches_plain_two_buffer_kernel(gpu_lib, nx, ny):
+    """FP32 periodic lattices take the TMA-fed persistent kernel; it gives the
+    plain two-buffer kernel's populations to FP32 rounding (the two kernels
+    contract the same expressions into FMAs differently: the measured gap is
+    one or two units in the last place) on full and partial tiles, lattices
+    narrower than the box and edge tiles whose halo wraps."""
+    r = np.random.default_rng(nx * 7 + ny)
+    pr = W.Problem("r", nx, ny, 0.5 + r.uniform(0.02, 1.0), 0.5 + r.uniform(0.02, 1.5),
+                   np.zeros((ny, nx)), np.zeros((ny, nx)), g=(1e-4, -2e-5))
+    f0 = W.random_populations(nx, ny, seed=nx + 3 * ny, amp=0.3)
+    A = gpu_lattice(pr, "f32", "current").set_f(f0)               # TMA (default)
+    B = gpu_lattice(pr, "f32", "current").set_kernel("scalar").set_f(f0)
+    for n in (1, 1, 4):
+        A.step(n)
+        B.step(n)
+        fa, fb = A.get_f(), B.get_f()
+        assert np.abs(fa - fb).max() <= 8 * np.finfo(np.float32).eps * np.abs(fb).max(), n
+
+
+def test_tma_wait_that_runs_out_is_reported(gpu_lib):
+    """A wait limit of 0 polls makes every tile wait give up: the step returns
+    early, the next read reports ETIMEOUT, and the context stays usable."""
+    from paper_2312_10318_gb300._lib import ETIMEOUT, TrtrlbError
+    pr = W.taylor_green(64, 0.04, 100.0, magic=0.25)
+    G = gpu_lattice(pr, "f32", "current").init(pr.ux, pr.uy, pr.rho)
+    G.set_wait_limit(0).step(1)
+    with pytest.raises(TrtrlbError) as e:
+        G.moments()
+    assert e.value.code == ETIMEOUT
+    G.set_wait_limit(1 << 22).init(pr.ux, pr.uy, pr.rho).step(10)
+    R = oracle_lattice(pr, "current").init(pr.ux, pr.uy, pr.rho)
+    R.step(10)
+    assert max(field_errors(G, R).values()) < 1e-5
