@@ -5,7 +5,23 @@
 #include "lb_device.cuh"
 #include "lb_ops.cuh"
 
+#include <type_traits>
+
 namespace trt {
+
+// Arithmetic of the import/export kernels (k_init, k_moments): FP64 for FP64
+// storage, double-word FP32 (about 48 significant bits, lb_dw.cuh) for every
+// other format, so that these kernels run on the FP32 pipes, which GB300 has
+// many times more of than FP64 ones.
+__device__ __forceinline__ void aux_round(df64 v, float& o) { o = __fadd_rn(v.hi, v.lo); }
+__device__ __forceinline__ void aux_round(df64 v, df64& o) { o = v; }
+__device__ __forceinline__ df64 aux_widen(float v) { return df64(v, 0.f); }
+__device__ __forceinline__ df64 aux_widen(const df64& v) { return v; }
+// c x for c in {-1, 0, 1} known at compile time once the loops are unrolled
+template <typename A>
+__device__ __forceinline__ A aux_sel(int c, const A& x) {
+    return c > 0 ? x : (c < 0 ? -x : A(0));
+}
 
 // Phi of non-fluid nodes (reading of the paper's silence on walls): 0 at
 // solid nodes, rho_w u_w^3 at moving-wall (inlet) nodes.  Both buffers.
@@ -41,7 +57,8 @@ __global__ void k_ghost_phi(const int* __restrict__ ghosts, int nghost, int nx, 
 // Initial state at an even level (reading of the paper's silence on
 // initialisation): f_i = f_i^eq(rho, u) - (1/2) w_i e_i.F / c_s^2 with the
 // third-order equilibrium of eq4 and F = rho g, so that sum f = rho and
-// sum e f = rho u - F/2 (eq11).  Arithmetic in FP64, rounded once to S.
+// sum e f = rho u - F/2 (eq11).  Arithmetic in FP64 (FP64 storage) or
+// double-word FP32 (the other formats), rounded once to S.
 // Also Phi = (rho u_x^3, rho u_y^3) into both buffers (Phi^{-1} := Phi^0).
 template <typename S>
 __global__ void k_init(Args<typename Fmt<S>::C> a, const double* __restrict__ rho,
@@ -60,26 +77,55 @@ __global__ void k_init(Args<typename Fmt<S>::C> a, const double* __restrict__ rh
         for (int i = 0; i < 9; ++i) F[(long long)i * a.plane + own] = Fmt<S>::st(C(0));
         return;
     }
-    const double r = rho ? rho[k] : rho0;
-    const double u = ux[k], v = uy[k];
-    const double t = 1.0 / 3.0;
+    if constexpr (std::is_same<S, double>::value) {
+        const double r = rho ? rho[k] : rho0;
+        const double u = ux[k], v = uy[k];
+        const double t = 1.0 / 3.0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const double cx = ex(i), cy = ey(i), w = wgt(i);
-        const double eu = cx * u + cy * v;
-        const double huu = (cx * cx - t) * u * u + 2.0 * cx * cy * u * v + (cy * cy - t) * v * v;
-        const double h3 = (cx * cx - t) * cy * u * u * v + (cy * cy - t) * cx * u * v * v;
-        const double feq = w * r * (1.0 + 3.0 * eu + 4.5 * huu + 13.5 * h3);
-        const double eF = r * (cx * gx + cy * gy);
-        F[(long long)i * a.plane + own] = Fmt<S>::st((C)(feq - 1.5 * w * eF - w * rho0));
+        for (int i = 0; i < 9; ++i) {
+            const double cx = ex(i), cy = ey(i), w = wgt(i);
+            const double eu = cx * u + cy * v;
+            const double huu = (cx * cx - t) * u * u + 2.0 * cx * cy * u * v + (cy * cy - t) * v * v;
+            const double h3 = (cx * cx - t) * cy * u * u * v + (cy * cy - t) * cx * u * v * v;
+            const double feq = w * r * (1.0 + 3.0 * eu + 4.5 * huu + 13.5 * h3);
+            const double eF = r * (cx * gx + cy * gy);
+            F[(long long)i * a.plane + own] = Fmt<S>::st((C)(feq - 1.5 * w * eF - w * rho0));
+        }
+        const C px = (C)(r * u * u * u), py = (C)(r * v * v * v);
+        a.phi_out[own] = px; a.phi_out[a.plane + own] = py;
+        phi_b[own] = px; phi_b[a.plane + own] = py;
+    } else {
+        // the same equilibrium, with the velocity products shared by the directions
+        using A = df64;
+        const A r = A(rho ? rho[k] : rho0);
+        const A u = A(ux[k]), v = A(uy[k]);
+        const A uu = u * u, vv = v * v, uv = u * v, uuv = uu * v, uvv = u * vv;
+        const A Fx = r * A(gx), Fy = r * A(gy), r0 = A(rho0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int cx = ex(i), cy = ey(i);
+            const double kx = cx * cx - 1.0 / 3.0, ky = cy * cy - 1.0 / 3.0, w = wgt(i);
+            const A eu = aux_sel(cx, u) + aux_sel(cy, v);
+            A huu = A(kx) * uu + A(ky) * vv;
+            if (cx * cy != 0) huu = huu + aux_sel(cx * cy, uv + uv);
+            const A h3 = aux_sel(cy, A(kx) * uuv) + aux_sel(cx, A(ky) * uvv);
+            const A feq = A(w) * r * (A(1) + A(3.0) * eu + A(4.5) * huu + A(13.5) * h3);
+            const A eF = aux_sel(cx, Fx) + aux_sel(cy, Fy);
+            C out;
+            aux_round(feq - A(1.5 * w) * eF - A(w) * r0, out);
+            F[(long long)i * a.plane + own] = Fmt<S>::st(out);
+        }
+        C px, py;
+        aux_round(r * uu * u, px);
+        aux_round(r * vv * v, py);
+        a.phi_out[own] = px; a.phi_out[a.plane + own] = py;
+        phi_b[own] = px; phi_b[a.plane + own] = py;
     }
-    const C px = (C)(r * u * u * u), py = (C)(r * v * v * v);
-    a.phi_out[own] = px; a.phi_out[a.plane + own] = py;
-    phi_b[own] = px; phi_b[a.plane + own] = py;
 }
 
 // FP64 moments (eq11) of a state of parity ODD into dense [ny][nx] arrays;
-// any output may be null; non-fluid nodes give 0.
+// any output may be null; non-fluid nodes give 0.  Computed in FP64 for FP64
+// storage and in double-word FP32 (about 48 bits) for the other formats.
 template <typename S, bool ODD>
 __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, double* uy) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,15 +144,27 @@ __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, d
     long long nb[9];
     int kind[9];
     links<true>(a, x, y, nb, kind);
-    double d[9];
+    if constexpr (std::is_same<S, double>::value) {
+        double d[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = (double)Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
-    if (c == PRESSURE) zh_fill<double>(d, (double)a.zh_dr);
-    double r, u, v;
-    moments_of<double>(d, (double)a.gx, (double)a.gy, (double)a.rho0, r, u, v);
-    if (rho) rho[k] = r;
-    if (ux) ux[k] = u;
-    if (uy) uy[k] = v;
+        for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]);
+        if (c == PRESSURE) zh_fill<double>(d, a.zh_dr);
+        double r, u, v;
+        moments_of<double>(d, a.gx, a.gy, a.rho0, r, u, v);
+        if (rho) rho[k] = r;
+        if (ux) ux[k] = u;
+        if (uy) uy[k] = v;
+    } else {
+        df64 d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = aux_widen(Fmt<S>::ld(F[pop_loc<ODD>(a.plane, nb, kind, i)]));
+        if (c == PRESSURE) zh_fill<df64>(d, aux_widen(a.zh_dr));
+        df64 r, u, v;
+        moments_of<df64>(d, aux_widen(a.gx), aux_widen(a.gy), aux_widen(a.rho0), r, u, v);
+        if (rho) rho[k] = (double)r;
+        if (ux) ux[k] = (double)u;
+        if (uy) uy[k] = (double)v;
+    }
 }
 
 // Export f_i(x, t) as FP64 [9][ny][nx] (non-fluid: 0) and Phi_in as [2][ny][nx].

@@ -21,7 +21,7 @@ namespace trt {
 struct df64 {
     float hi, lo;
 
-    __host__ __device__ df64() : hi(0.f), lo(0.f) {}
+    df64() = default;   // trivial, so that __shared__ arrays of pairs need no constructor
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ df64(int v) : hi((float)v), lo(0.f) {}
     // split of a double: hi = fl32(x), lo = fl32(x - hi); exact to ~2^-48 |x|

@@ -47,12 +47,17 @@ def test_create_rejects_invalid_parameters_before_touching_the_device(lib):
     p = _lib.Params()
     lib.trtrlb_default_params(C.byref(p))
     h = C.c_void_p()
-    bad = [("tau_s", 0.5), ("nx", 0), ("storage", 9), ("g_mode", 7), ("rho0", -1.0)]
+    bad = [("tau_s", 0.5), ("nx", 0), ("storage", 9), ("g_mode", 7), ("rho0", -1.0),
+           ("nx", (1 << 24) + 1), ("ny", 131071)]
     for field, val in bad:
         q = _lib.Params()
         C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
         setattr(q, field, val)
         assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL, field
+    q = _lib.Params()
+    C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+    q.nx, q.ny = 1 << 24, 64                 # (nx + 63) * ny above 2^30
+    assert lib.trtrlb_create(C.byref(q), None, None, C.byref(h)) == _lib.EINVAL
     q = _lib.Params()
     C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
     q.tau_s2, q.magic = 0.4999, float("nan")     # tau_s2 = 1/2 is the smallest accepted
