@@ -141,7 +141,7 @@ __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, d
         if (uy) uy[k] = 0.0;
         return;
     }
-    long long nb[9];
+    int nb[9];
     int kind[9];
     links<true>(a, x, y, nb, kind);
     if constexpr (std::is_same<S, double>::value) {
@@ -187,7 +187,7 @@ __global__ void k_get_f(Args<typename Fmt<S>::C> a, double* f, double* phi) {
         for (int i = 0; i < 9; ++i) f[i * n + k] = 0.0;
         return;
     }
-    long long nb[9];
+    int nb[9];
     int kind[9];
     links<true>(a, x, y, nb, kind);
     double d[9];
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Args<typename Fmt
         const long long own = (long long)y * a.pitch + x;
         const int c = a.mask ? a.mask[own] : FLUID;
         if (!collides(c)) continue;
-        long long nb[9];
+        int nb[9];
         int kind[9];
         links<true>(a, x, y, nb, kind);
         double d[9];

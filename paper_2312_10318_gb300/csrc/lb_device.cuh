@@ -121,14 +121,14 @@ __device__ __forceinline__ Nbh neighbours(const Args<C>& a, int x, int y) {
     return n;
 }
 
-// Linear index (within a plane) of x + e_i and whether it lies outside.
+// Linear index (within a plane, < 2^30) of x + e_i and whether it lies outside.
 template <int I>
-__device__ __forceinline__ long long nb_index(const Nbh& n, int x, int y, int pitch, bool& out) {
+__device__ __forceinline__ int nb_index(const Nbh& n, int x, int y, int pitch, bool& out) {
     constexpr int dx = ex(I), dy = ey(I);
     const int cx = dx > 0 ? n.xp : (dx < 0 ? n.xm : x);
     const int cy = dy > 0 ? n.yp : (dy < 0 ? n.ym : y);
     out = (dx > 0 && n.oxp) || (dx < 0 && n.oxm) || (dy > 0 && n.oyp) || (dy < 0 && n.oym);
-    return (long long)cy * pitch + cx;
+    return cy * pitch + cx;
 }
 
 __device__ __forceinline__ int kind_of(uint8_t c) {
@@ -137,11 +137,11 @@ __device__ __forceinline__ int kind_of(uint8_t c) {
 
 // Link kinds of the 8 neighbours x + e_i (index 0 unused) and their indices.
 template <bool GENERAL, typename C>
-__device__ __forceinline__ void links(const Args<C>& a, int x, int y, long long (&nb)[9],
+__device__ __forceinline__ void links(const Args<C>& a, int x, int y, int (&nb)[9],
                                       int (&kind)[9]) {
     const Nbh n = neighbours(a, x, y);
     bool out[9];
-    nb[0] = (long long)y * a.pitch + x;
+    nb[0] = y * a.pitch + x;
     kind[0] = K_STREAM;
     out[0] = false;
 #define TRT_NB(I) nb[I] = nb_index<I>(n, x, y, a.pitch, out[I]);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void links(const Args<C>& a, int x, int y, long long 
 
 // Location (offset into F) of f_i(x, t) for a state whose level has parity ODD.
 template <bool ODD>
-__device__ __forceinline__ long long pop_loc(long long plane, const long long (&nb)[9],
+__device__ __forceinline__ long long pop_loc(long long plane, const int (&nb)[9],
                                              const int (&kind)[9], int i) {
     if (!ODD) return (long long)i * plane + nb[0];
     const int j = opp(i);  // x - e_i = x + e_j
@@ -285,10 +285,10 @@ template <typename S, bool ODD, bool GENERAL, int GMODE>
 __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int x, int y) {
     using C = typename Fmt<S>::C;
     S* __restrict__ F = static_cast<S*>(a.f);
-    const long long own = (long long)y * a.pitch + x;
+    const int own = y * a.pitch + x;   // in-plane offsets stay below 2^30
     const int cls = (GENERAL && a.mask) ? a.mask[own] : FLUID;
     if (GENERAL && !collides(cls)) return;
-    long long nb[9];
+    int nb[9];
     int kind[9];
     links<GENERAL>(a, x, y, nb, kind);
 
@@ -304,10 +304,10 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
         const C* Py = a.phi_in + a.plane;
         // beyond a pressure outlet Phi continues with zero gradient
         const C pxp = (GENERAL && n.oxp) ? (cls == PRESSURE ? Px[own] : C(0))
-                                         : Px[(long long)y * a.pitch + n.xp];
-        const C pxm = (GENERAL && n.oxm) ? C(0) : Px[(long long)y * a.pitch + n.xm];
-        const C pyp = (GENERAL && n.oyp) ? C(0) : Py[(long long)n.yp * a.pitch + x];
-        const C pym = (GENERAL && n.oym) ? C(0) : Py[(long long)n.ym * a.pitch + x];
+                                         : Px[y * a.pitch + n.xp];
+        const C pxm = (GENERAL && n.oxm) ? C(0) : Px[y * a.pitch + n.xm];
+        const C pyp = (GENERAL && n.oyp) ? C(0) : Py[n.yp * a.pitch + x];
+        const C pym = (GENERAL && n.oym) ? C(0) : Py[n.ym * a.pitch + x];
         dpx = C(0.5) * (pxp - pxm);
         dpy = C(0.5) * (pyp - pym);
     }
@@ -351,7 +351,7 @@ __global__ void k_ghosts(Args<typename Fmt<S>::C> a, const int* __restrict__ gho
     const int sx = s % a.pitch, sy = s / a.pitch;
     int zx = sx - 1;
     if (zx < 0) zx += a.nx;  // validated: inside the domain (periodic) and fluid
-    long long nbs[9], nbz[9];
+    int nbs[9], nbz[9];
     int ks[9], kz[9];
     links<true>(a, sx, sy, nbs, ks);
     links<true>(a, zx, sy, nbz, kz);
@@ -369,7 +369,7 @@ __global__ void k_ghosts(Args<typename Fmt<S>::C> a, const int* __restrict__ gho
         // location of f_i(x) in the new state, x = s + e_i
         const long long x_lin = nbs[i];
         const int xx = (int)(x_lin % a.pitch), xy = (int)(x_lin / a.pitch);
-        long long nbx[9];
+        int nbx[9];
         int kx[9];
         links<true>(a, xx, xy, nbx, kx);
         const long long dst = ODD_NEW ? pop_loc<true>(a.plane, nbx, kx, i)
