@@ -21,7 +21,7 @@ template <typename C, int MAXL> struct GroupParams {
 };
 
 template <typename S, bool ODD, bool GENERAL, int GMODE, int MAXL>
-__global__ void __launch_bounds__(BATCH_THREADS)
+__global__ void __launch_bounds__(BATCH_THREADS, step_min_blocks<S, GENERAL, GMODE>())
     k_step_group(const __grid_constant__ GroupParams<typename Fmt<S>::C, MAXL> p) {
     const int b = (int)blockIdx.x;
     int lo = 0, hi = p.n - 1;

@@ -135,11 +135,23 @@ __device__ __forceinline__ int kind_of(uint8_t c) {
     return c == SOLID ? K_WALL : (c == INLET ? K_MOVING : K_STREAM);
 }
 
+// Neighbourhood of a node of a lattice periodic in x and y (no flags needed).
+template <typename C>
+__device__ __forceinline__ Nbh neighbours_periodic(const Args<C>& a, int x, int y) {
+    Nbh n;
+    n.xm = x == 0 ? a.nx - 1 : x - 1;
+    n.xp = x == a.nx - 1 ? 0 : x + 1;
+    n.ym = y == 0 ? a.ny - 1 : y - 1;
+    n.yp = y == a.ny - 1 ? 0 : y + 1;
+    n.oxm = n.oxp = n.oym = n.oyp = false;
+    return n;
+}
+
 // Link kinds of the 8 neighbours x + e_i (index 0 unused) and their indices.
 template <bool GENERAL, typename C>
 __device__ __forceinline__ void links(const Args<C>& a, int x, int y, int (&nb)[9],
                                       int (&kind)[9]) {
-    const Nbh n = neighbours(a, x, y);
+    const Nbh n = GENERAL ? neighbours(a, x, y) : neighbours_periodic(a, x, y);
     bool out[9];
     nb[0] = y * a.pitch + x;
     kind[0] = K_STREAM;
@@ -277,6 +289,15 @@ __device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, 
 
 // ---- kernels ----------------------------------------------------------------
 
+// Resident 256-thread CTAs per SM the scalar step kernels ask the compiler to
+// allow: the FP32 periodic step with lagged G fits 40 registers without
+// spilling (6 CTAs, 75 % occupancy for the odd step instead of 5); the other
+// variants keep the compiler's choice.
+template <typename S, bool GENERAL, int GMODE>
+__host__ __device__ constexpr int step_min_blocks() {
+    return (sizeof(S) == 4 && !GENERAL && GMODE == G_LAGGED) ? 6 : 1;
+}
+
 // One fused AA step of one node (pull-stream, moments, regularized TRT
 // collision, G_i, F_i, push-back into the same slots, half-way bounce-back);
 // non-fluid nodes return at once.  GENERAL enables walls, masks and
@@ -299,7 +320,7 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
 
     C dpx = C(0), dpy = C(0);
     if (GMODE == G_LAGGED) {
-        const Nbh n = neighbours(a, x, y);
+        const Nbh n = GENERAL ? neighbours(a, x, y) : neighbours_periodic(a, x, y);
         const C* Px = a.phi_in;
         const C* Py = a.phi_in + a.plane;
         // beyond a pressure outlet Phi continues with zero gradient
@@ -331,7 +352,7 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
 }
 
 template <typename S, bool ODD, bool GENERAL, int GMODE>
-__global__ void __launch_bounds__(256) k_step(Args<typename Fmt<S>::C> a) {
+__global__ void __launch_bounds__(256, step_min_blocks<S, GENERAL, GMODE>()) k_step(Args<typename Fmt<S>::C> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
