@@ -17,8 +17,24 @@ template <typename C, int MAXL> struct GroupParams {
     int tiles_x[MAXL];           // tiles per tile row
     int log2_tw[MAXL];           // scalar: tile width 2^log2_tw nodes, height 256 / width
     int segs[MAXL];              // vector: warp segments per row
+    float inv_d[MAXL];           // 1 / tiles_x (scalar) or 1 / segs (vector), rounded
     Args<C> a[MAXL];
 };
+
+// q = t / d and r = t % d for 0 <= t < 2^24 and d >= 1, from the rounded
+// reciprocal inv = 1/d: the float estimate of t/d is within 2^-23 relative,
+// so its truncation is off by at most one, which one compare corrects.
+__device__ __forceinline__ void tile_divmod(int t, int d, float inv, int& q, int& r) {
+    q = __float2int_rz(__fmul_rn((float)t, inv));
+    r = t - q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
+    }
+}
 
 template <typename S, bool ODD, bool GENERAL, int GMODE, int MAXL>
 __global__ void __launch_bounds__(BATCH_THREADS, step_min_blocks<S, GENERAL, GMODE>())
@@ -32,7 +48,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, step_min_blocks<S, GENERAL, GMO
     }
     const int lt = p.log2_tw[lo];
     const int t = b - p.tile_begin[lo];
-    const int tx = t % p.tiles_x[lo], ty = t / p.tiles_x[lo];
+    int tx, ty;
+    tile_divmod(t, p.tiles_x[lo], p.inv_d[lo], ty, tx);
     const int x = (tx << lt) + ((int)threadIdx.x & ((1 << lt) - 1));
     const int y = (ty << (8 - lt)) + ((int)threadIdx.x >> lt);
     if (x >= p.a[lo].nx || y >= p.a[lo].ny) return;
@@ -52,11 +69,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(S) == 2 ? 4 : 3)
         else hi = mid - 1;
     }
     const int lane = (int)threadIdx.x & 31;
-    const long long s = (long long)(b - p.tile_begin[lo]) * 8 + ((int)threadIdx.x >> 5);
+    const int s = (b - p.tile_begin[lo]) * 8 + ((int)threadIdx.x >> 5);   // < 2^24
     const int spr = p.segs[lo];
-    if (s >= (long long)spr * p.a[lo].ny) return;   // whole warp leaves together
-    const int y = (int)(s / spr);
-    const int x0 = (int)(s % spr) * 32 * V + lane * V;
+    if ((long long)s >= (long long)spr * p.a[lo].ny) return;   // whole warp leaves together
+    int y, sx;
+    tile_divmod(s, spr, p.inv_d[lo], y, sx);
+    const int x0 = sx * 32 * V + lane * V;
     seg_step<S, ODD, GMODE>(p.a[lo], x0, y, lane);
 }
 

@@ -238,6 +238,7 @@ static cudaError_t launch_group(const State* const* m, const int* cur, const int
         p.tile_begin[q] = tiles;
         if (FLAV == FLAV_VECTOR) {
             p.segs[q] = (v.nx + 32 * V - 1) / (32 * V);
+            p.inv_d[q] = 1.0f / (float)p.segs[q];
             p.tiles_x[q] = 0;
             p.log2_tw[q] = 0;
             tiles += (int)(((long long)p.segs[q] * v.ny + 7) / 8);
@@ -246,6 +247,7 @@ static cudaError_t launch_group(const State* const* m, const int* cur, const int
             p.log2_tw[q] = l2tw[q];
             p.segs[q] = 0;
             p.tiles_x[q] = (v.nx + tw - 1) / tw;
+            p.inv_d[q] = 1.0f / (float)p.tiles_x[q];
             tiles += p.tiles_x[q] * ((v.ny + th - 1) / th);
         }
     }
