@@ -13,6 +13,7 @@
 // f*_i to F[i][x + e_i] (or F[ibar][x] at a wall), which are the same nine
 // locations, so the update is in place and race-free.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -195,10 +196,94 @@ __device__ __forceinline__ long long pop_loc(long long plane, const int (&nb)[9]
 // weights w_i are folded into the coefficients below.  The raw moments share
 // their partial sums (the compiler may not reassociate float additions).
 // Returns Phi_xxx = rho u_x^3 and Phi_yyy = rho u_y^3 of the node (eq11 u).
+//
+// collide_dw: the same collision for double-word pairs, arranged for fewer
+// double-word operations (each costs 8-11 FP32 instructions, and this format
+// is bound by them): scalings by powers of two are exact per component, the
+// reconstruction shares b9 = drho/9, h = a2/3 and g = a1/3 (5 products by
+// constants instead of 16), the reciprocal is taken directly, and without a
+// body force (a uniform branch) the forcing terms are skipped -- they would
+// add exact zeros.
+__device__ __forceinline__ df64 scale2(const df64& x, float p) {   // p a power of two
+    return df64(__fmul_rn(x.hi, p), __fmul_rn(x.lo, p));
+}
+
+__device__ __forceinline__ void collide_dw(const df64 (&d)[9], df64 dpx, df64 dpy, const df64 k1,
+                                           const df64 k2, const df64 kf, const df64 gx,
+                                           const df64 gy, const df64 rho0, df64 (&o)[9], df64& phx,
+                                           df64& phy) {
+    const df64 third = df64(1.0 / 3.0);
+    const df64 s13 = d[1] + d[3], m13 = d[1] - d[3];
+    const df64 s24 = d[2] + d[4], m24 = d[2] - d[4];
+    const df64 a57 = d[5] + d[7], m57 = d[5] - d[7];
+    const df64 a68 = d[6] + d[8], m68 = d[6] - d[8];
+    const df64 sd = a57 + a68, pxy = a57 - a68;
+    const df64 qxxy = m57 + m68, qxyy = m57 - m68;
+    const df64 jx = m13 + qxyy, jy = m24 + qxxy;
+    const df64 drho = (d[0] + sd) + (s13 + s24);
+    const df64 rho = rho0 + drho;
+    const df64 inv = recip(rho);
+    const bool forced = gx.hi != 0.f || gx.lo != 0.f || gy.hi != 0.f || gy.lo != 0.f;
+    df64 ux = jx * inv, uy = jy * inv;
+    if (forced) {
+        ux = ux + scale2(gx, 0.5f);
+        uy = uy + scale2(gy, 0.5f);
+    }
+    const df64 rux = rho * ux, ruy = rho * uy;
+    const df64 ruxx = rux * ux, ruyy = ruy * uy, ruxy = rux * uy;
+    const df64 rxxy = ruxx * uy, rxyy = ruyy * ux;
+    const df64 drho3 = third * drho;
+    const df64 Axx = ((s13 + sd) - drho3) - ruxx, Ayy = ((s24 + sd) - drho3) - ruyy;
+    const df64 Axy = pxy - ruxy;
+    const df64 Axxy = (qxxy - third * jy) - rxxy, Axyy = (qxyy - third * jx) - rxyy;
+    df64 a1x = jx, a1y = jy;
+    df64 a2xx = (ruxx + k1 * Axx) - kf * dpx;
+    df64 a2yy = (ruyy + k1 * Ayy) - kf * dpy;
+    df64 a2xy = ruxy + k1 * Axy;
+    if (forced) {
+        const df64 Fx = rho * gx, Fy = rho * gy;
+        a1x = a1x + Fx;
+        a1y = a1y + Fy;
+        a2xx = a2xx + kf * scale2(Fx * ux, 2.f);
+        a2yy = a2yy + kf * scale2(Fy * uy, 2.f);
+        a2xy = a2xy + kf * (Fx * uy + ux * Fy);
+    }
+    const df64 a3xxy = rxxy + k2 * Axxy, a3xyy = rxyy + k2 * Axyy;
+    // reconstruction with the weights folded in (see collide)
+    const df64 b9 = third * drho3;                   // drho / 9
+    const df64 hxx = third * a2xx, hyy = third * a2yy;
+    const df64 g1x = third * a1x, g1y = third * a1y;
+    const df64 ht = hxx + hyy;                       // (a2xx + a2yy) / 3
+    o[0] = scale2(b9, 4.f) - scale2(ht, 2.f);
+    const df64 c13 = (b9 + hxx) - scale2(hyy, 0.5f);
+    const df64 c24 = (b9 + hyy) - scale2(hxx, 0.5f);
+    const df64 o13 = g1x - scale2(a3xyy, 0.5f);
+    const df64 o24 = g1y - scale2(a3xxy, 0.5f);
+    o[1] = c13 + o13;
+    o[3] = c13 - o13;
+    o[2] = c24 + o24;
+    o[4] = c24 - o24;
+    const df64 cd = scale2(b9 + ht, 0.25f);
+    const df64 q = scale2(a2xy, 0.25f);
+    const df64 c57 = cd + q, c68 = cd - q;
+    const df64 o57 = scale2((g1x + g1y) + (a3xxy + a3xyy), 0.25f);
+    const df64 o68 = scale2((g1y - g1x) + (a3xxy - a3xyy), 0.25f);
+    o[5] = c57 + o57;
+    o[7] = c57 - o57;
+    o[6] = c68 + o68;
+    o[8] = c68 - o68;
+    phx = ruxx * ux;
+    phy = ruyy * uy;
+}
+
 template <typename C>
 __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k1lo,
                                         const C k2, const C k2lo, const C kf, const C gx,
                                         const C gy, const C rho0, C (&o)[9], C& phx, C& phy) {
+    if constexpr (std::is_same<C, df64>::value) {
+        collide_dw(d, dpx, dpy, k1, k2, kf, gx, gy, rho0, o, phx, phy);
+        return;
+    } else {
     const C third = C(1.0 / 3.0);
     // raw moments of the shifted populations
     const C s13 = d[1] + d[3], m13 = d[1] - d[3];
@@ -272,6 +357,7 @@ __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k
     o[8] = c68 - o68;
     phx = ruxx * ux;
     phy = ruyy * uy;
+    }
 }
 
 // Moments of one node from shifted populations (eq11).
