@@ -198,11 +198,15 @@ class PrecisionGuard:
     format's stated bound, else `tol`) the solve moves to the next wider format
     (FP16/BF16 -> FP32 -> FP64), which is checked the same way; FP64 needs no
     check.  The kept lattice restarts at t = 0.  Call it with the lattice's
-    stream current (the server does): the probe's fields live on that stream."""
+    stream current (the server does): the probe's fields live on that stream.
+    The FP64 shadow, and the last fallback, use the storage `fp64` ("f64", or
+    "f64dw": FP64-level results from FP32 instructions); a Server sets it to its
+    own fp64_as."""
 
-    def __init__(self, tol: Optional[float] = None, probe: int = 64):
+    def __init__(self, tol: Optional[float] = None, probe: int = 64, fp64: str = "f64"):
         self.tol = tol
         self.probe = probe
+        self.fp64 = fp64
         self.checked = []      # (rid, storage, e_end, predicted, tol)
 
     @staticmethod
@@ -231,7 +235,8 @@ class PrecisionGuard:
         sp = spec_of(req)
         scale = velocity_scale(sp)
         fields = device_fields(req, sp)
-        shadow = Lattice(sp.nx, sp.ny, sp.tau_s, storage="f64", stream=lat._stream, **sp.lattice_kwargs())
+        shadow = Lattice(sp.nx, sp.ny, sp.tau_s, storage=self.fp64, stream=lat._stream,
+                         **sp.lattice_kwargs())
         storage, cur = req.storage, lat
         while storage != "f64":
             tol = self.tol if self.tol is not None else STATED_BOUND[storage]
@@ -303,6 +308,8 @@ class Server:
         self.max_active_nodes = float(max_active_nodes)
         self.tuner = tuner            # autotuner applied to every admitted lattice
         self.fp64_as = fp64_as        # format FP64 requests run in: "f64" or "f64dw"
+        if guard is not None and hasattr(guard, "fp64"):
+            guard.fp64 = fp64_as      # the guard's shadow and last fallback use it too
         self.active_nodes = 0
         self.used = 0
         self.node_updates = 0

@@ -144,3 +144,14 @@ def test_fp64_requests_in_double_word_format(gpu_lib):
         (f64, _), _ = _alone(req)
         rel = np.abs(final[req.rid] - f64).max() / np.abs(f64).max()
         assert rel < 1e-11, (req, rel)
+
+
+def test_precision_guard_falls_back_to_the_servers_fp64_format(gpu_lib):
+    """With fp64_as="f64dw" the guard's shadow and its last fallback use the
+    double-word format, so a widened solve does not drop to native FP64 speed."""
+    reqs = [S.Request(0, "taylor_green", 64, 100.0, 200, "f16"),
+            S.Request(1, "double_shear_layer", 64, 1e4, 200, "f32")]
+    strict = S.PrecisionGuard(tol=1e-12, probe=16)
+    res = S.Server(chunk=64, guard=strict, fp64_as="f64dw").run(reqs, realtime=False)
+    assert all(r.fallback and r.storage == "f64dw" and r.status == "ok" for r in res)
+    assert strict.fp64 == "f64dw"
