@@ -529,7 +529,7 @@ const char* trtrlb_strerror(int code) {
         case TRTRLB_ECUDA: return "CUDA error";
         case TRTRLB_EUNSTABLE: return "unstable state (NaN/Inf or velocity bound exceeded)";
         case TRTRLB_ETIMEOUT: return "bounded wait timed out";
-        case TRTRLB_ENOTSUP: return "not supported by this build";
+        case TRTRLB_ENOTSUP: return "not supported";
         default: return "unknown error";
     }
 }
