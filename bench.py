@@ -88,6 +88,26 @@ def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
     return b
 
 
+# FP64 storage runs its collision on GB300's FP64 pipe, which bounds it long
+# before HBM does: its roofline is arithmetic.  128 FP64 operations per node
+# update, counted from the collision and the central differences of the step
+# (add, multiply and divide each 1; a fused multiply-add replaces two); the
+# peak is GB300's nominal dense FP64 rate (no FP64 rate is measured on the pool).
+FP64_OPS_PER_NODE = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def alu_roofline(storage: str, nodes_per_launch: float, launch_s: float):
+    """The arithmetic roofline of an FP64-storage step, or None for the formats
+    whose step is bound by memory traffic."""
+    if storage != "f64":
+        return None
+    achieved = FP64_OPS_PER_NODE * nodes_per_launch / launch_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64 (not measured)",
+            "traffic": None, "ops_per_node": FP64_OPS_PER_NODE}
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -509,12 +529,11 @@ def main():
                                  else "one kernel per lattice and time step",
                        "l2": f"{args.flush_mib} MiB written then read before every timed step "
                              "(outside the events)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": alu_roofline(storage, nodes / per_step_launches, launch_s) or
+                        {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic is None else traffic,
-                         "kernel": kernel_label(args, lats[0].kernel()[0]),
-                         "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode),
-                         "launch_ms": launch_s * 1e3},
+                         "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": field_bytes / args.e2e_steps,
                     "d2h_bytes_per_step": field_bytes / args.e2e_steps,
@@ -522,6 +541,9 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
         }
+        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0])
+        line["roofline"]["launch_ms"] = launch_s * 1e3
+        line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(problems)
         if not args.no_serve:
