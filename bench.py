@@ -21,6 +21,7 @@ import argparse
 import glob
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -511,6 +512,8 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = max_over_ranks(statistics.median(e2e_times) if e2e_times else float("nan"), dist)
     e2e_value = whole_job_rate(nodes * args.e2e_steps, world, e2e_t) / 1e6
+    if not math.isfinite(e2e_value):
+        e2e_value = None          # --no-e2e: no end-to-end number (null, not NaN, in the JSON)
     field_bytes = 3 * 8 * nodes
 
     if rank == 0:
