@@ -216,6 +216,19 @@ int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx,
 #define TRTRLB_KERNEL_VECTOR 2
 int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w);
 
+/* Checkpoint and resume (the paper has none): the raw device state -- the
+ * populations as stored (format, AA level and layout), both Phi buffers, the
+ * level's parity, the Phi buffer index and the step count -- as an opaque
+ * image of trtrlb_state_bytes(h) bytes in host or device memory.  Loading it
+ * into a lattice created with the same parameters and mask continues bit for
+ * bit as the saved one would have (trtrlb_get_f / trtrlb_set_f go through
+ * FP64 and the shift by w_i rho0, which rounds for FP64 storage).  Both
+ * synchronise the handle's stream.  trtrlb_load returns EINVAL for an image of
+ * another size, format or G mode. */
+int64_t trtrlb_state_bytes(trtrlb_t h);
+int trtrlb_save(trtrlb_t h, void* image);
+int trtrlb_load(trtrlb_t h, const void* image);
+
 /* Bounded waits.  The TMA-fed G_CURRENT kernel (FP32, periodic, no mask)
  * waits on an mbarrier for each tile copy; after `polls` unsuccessful polls
  * (default 4,194,304: far beyond a copy's microseconds) it records the failure,

@@ -53,6 +53,9 @@ SIGNATURES = {
     "trtrlb_set_kernel": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "trtrlb_get_kernel": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "trtrlb_set_wait_limit": (C.c_int, [_vp, _i64]),
+    "trtrlb_state_bytes": (C.c_int64, [_vp]),
+    "trtrlb_save": (C.c_int, [_vp, _vp]),
+    "trtrlb_load": (C.c_int, [_vp, _vp]),
     "trtrlb_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "trtrlb_batch_set": (C.c_int, [_vp, C.POINTER(_vp), C.c_int]),
     "trtrlb_batch_step": (C.c_int, [_vp, _i64]),

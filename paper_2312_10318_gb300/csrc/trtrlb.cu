@@ -439,6 +439,66 @@ int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
     return host ? check_kerr(h) : TRTRLB_OK;
 }
 
+// ---- checkpoint image -------------------------------------------------------
+namespace {
+
+struct ImageHeader {
+    uint64_t magic;                   // "TRTRLBS1"
+    int32_t nx, ny, storage, g_mode;
+    int32_t parity, cur, pitch, reserved;
+    int64_t t;
+};
+constexpr uint64_t kImageMagic = 0x3153424c52545254ull;   // bytes "TRTRLBS1"
+
+size_t image_pop_bytes(const trtrlb_lattice* h) { return elem_size(h->p.storage) * 9 * (size_t)h->s.plane; }
+size_t image_phi_bytes(const trtrlb_lattice* h) { return phi_size(h->p.storage) * 4 * (size_t)h->s.plane; }
+
+}  // namespace
+
+int64_t trtrlb_state_bytes(trtrlb_t h) {
+    if (!h) return -1;
+    return (int64_t)(sizeof(ImageHeader) + image_pop_bytes(h) + image_phi_bytes(h));
+}
+
+int trtrlb_save(trtrlb_t h, void* image) {
+    if (!h || !image) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    ImageHeader hd{kImageMagic, h->p.nx, h->p.ny, h->p.storage, h->p.g_mode,
+                   h->s.parity, h->s.cur, h->s.pitch, 0, h->t};
+    char* out = static_cast<char*>(image);
+    cudaError_t e = cudaMemcpyAsync(out, &hd, sizeof hd, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + sizeof hd, h->s.f, image_pop_bytes(h), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + sizeof hd + image_pop_bytes(h), h->phi, image_phi_bytes(h),
+                            cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "save");
+    return TRTRLB_OK;
+}
+
+int trtrlb_load(trtrlb_t h, const void* image) {
+    if (!h || !image) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    const char* in = static_cast<const char*>(image);
+    ImageHeader hd;
+    cudaError_t e = cudaMemcpy(&hd, in, sizeof hd, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "load");
+    if (hd.magic != kImageMagic || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.storage != h->p.storage ||
+        hd.g_mode != h->p.g_mode || hd.pitch != h->s.pitch || (hd.parity & ~1) || (hd.cur & ~1))
+        return fail(h->err, TRTRLB_EINVAL, "state image does not match this lattice");
+    e = cudaMemcpyAsync(h->s.f, in + sizeof hd, image_pop_bytes(h), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->phi, in + sizeof hd + image_pop_bytes(h), image_phi_bytes(h),
+                            cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "load");
+    h->s.parity = hd.parity;
+    h->s.cur = hd.cur;
+    h->t = hd.t;
+    return TRTRLB_OK;
+}
+
 int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi) {
     if (!h) return TRTRLB_EINVAL;
     h->err[0] = 0;

@@ -148,6 +148,21 @@ class Lattice:
         self._chk(self._lib.trtrlb_set_kernel(self._h, v, int(tile_w)))
         return self
 
+    def save(self) -> np.ndarray:
+        """Checkpoint: the raw state image (uint8 host array) for load()."""
+        buf = np.empty(int(self._lib.trtrlb_state_bytes(self._h)), np.uint8)
+        self._chk(self._lib.trtrlb_save(self._h, buf.ctypes.data))
+        return buf
+
+    def load(self, image: np.ndarray):
+        """Resume from an image of save() taken on a lattice with the same
+        parameters and mask (bit for bit)."""
+        image = np.ascontiguousarray(image, np.uint8)
+        if image.size != int(self._lib.trtrlb_state_bytes(self._h)):
+            raise ValueError("state image size does not match this lattice")
+        self._chk(self._lib.trtrlb_load(self._h, image.ctypes.data))
+        return self
+
     def set_wait_limit(self, polls: int):
         """Polls before a kernel's bounded wait gives up (0: at once)."""
         self._chk(self._lib.trtrlb_set_wait_limit(self._h, int(polls)))

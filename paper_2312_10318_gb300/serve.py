@@ -49,7 +49,7 @@ class Request:
 @dataclass
 class Result:
     rid: int
-    status: str               # "ok" | "unstable" | "rejected"
+    status: str               # "ok" | "unstable" | "rejected" | "cancelled"
     storage: str              # storage the solve finished in
     steps: int
     diagnostics: dict
@@ -308,6 +308,7 @@ class Server:
         self.max_active_nodes = float(max_active_nodes)
         self.tuner = tuner            # autotuner applied to every admitted lattice
         self.fp64_as = fp64_as        # format FP64 requests run in: "f64" or "f64dw"
+        self._cancelled = set()       # request ids to drop (see cancel)
         if guard is not None and hasattr(guard, "fp64"):
             guard.fp64 = fp64_as      # the guard's shadow and last fallback use it too
         self.active_nodes = 0
@@ -358,6 +359,13 @@ class Server:
         return Result(a.req.rid, status, a.storage, a.req.steps - a.remaining, diag, a.req.arrival,
                       a.t_admit, now, a.fallback)
 
+    def cancel(self, rid: int):
+        """Drops request `rid`: a waiting one never starts; an active one is
+        retired as "cancelled" (with its partial diagnostics) at the end of the
+        current chunk, and its device memory is freed.  Callable from another
+        thread or from an on_retire callback while run() serves."""
+        self._cancelled.add(rid)
+
     def _unstable(self, d: dict) -> bool:
         return d["nonfinite"] > 0 or not math.isfinite(d["max_u"]) or d["max_u"] > self.max_u
 
@@ -374,6 +382,9 @@ class Server:
             now = clock()
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.pop(0))
+            for req in [r for r in waiting if r.rid in self._cancelled]:
+                waiting.remove(req)
+                results.append(Result(req.rid, "cancelled", req.storage, 0, {}, req.arrival, now, now))
             # admission, first come first served
             while waiting:
                 req = waiting[0]
@@ -405,6 +416,9 @@ class Server:
             check = self.check_every > 0 and chunks % self.check_every == 0
             keep = []
             for a in active:
+                if a.req.rid in self._cancelled and a.remaining > 0:
+                    results.append(self._retire(a, now, "cancelled", a.lat.diagnostics()))
+                    continue
                 if a.remaining == 0 or check:
                     d = a.lat.diagnostics()
                     if self._unstable(d):
@@ -470,6 +484,7 @@ def summarize(results: list, makespan: float, node_updates: Optional[float] = No
             "unstable": sum(r.status == "unstable" for r in results),
             "rejected": sum(r.status == "rejected" for r in results),
             "fallbacks": sum(r.fallback for r in results),
+            "cancelled": sum(r.status == "cancelled" for r in results),
             "makespan_s": makespan, "solves_per_s": len(done) / makespan if makespan > 0 else float("nan"),
             "mlups": node_updates / makespan / 1e6 if makespan > 0 else float("nan"),
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}

@@ -155,3 +155,30 @@ def test_precision_guard_falls_back_to_the_servers_fp64_format(gpu_lib):
     res = S.Server(chunk=64, guard=strict, fp64_as="f64dw").run(reqs, realtime=False)
     assert all(r.fallback and r.storage == "f64dw" and r.status == "ok" for r in res)
     assert strict.fp64 == "f64dw"
+
+
+def test_cancelled_requests_free_their_memory_and_leave_the_rest_alone(gpu_lib):
+    """A waiting request cancelled before it starts never runs; an active one is
+    retired at the next chunk boundary; the device budget returns to zero and
+    every other solve equals the same solve run alone."""
+    reqs = [S.Request(0, "taylor_green", 48, 100.0, 64, "f32"),
+            S.Request(1, "double_shear_layer", 96, 1e4, 2000, "f32"),
+            S.Request(2, "taylor_green", 64, 50.0, 300, "f64"),
+            S.Request(3, "poiseuille", 32, 10.0, 200, "f16")]
+    srv = None
+
+    def on_retire(req, lat, status):
+        if req.rid == 0:
+            srv.cancel(1)          # mid-flight: request 1 is active when 0 finishes
+
+    srv = S.Server(chunk=32, on_retire=on_retire)
+    srv.cancel(3)                  # before it starts
+    res = {r.rid: r for r in srv.run(reqs, realtime=False)}
+    assert res[3].status == "cancelled" and res[3].steps == 0
+    assert res[1].status == "cancelled" and 0 < res[1].steps < 2000
+    assert res[0].status == "ok" and res[2].status == "ok"
+    assert srv.used == 0 and srv.active_nodes == 0
+    for rid in (0, 2):
+        assert res[rid].diagnostics == _alone(reqs[rid])[1]
+    s = S.summarize(list(res.values()), srv.makespan, srv.node_updates)
+    assert s["cancelled"] == 2 and s["completed"] == 2
