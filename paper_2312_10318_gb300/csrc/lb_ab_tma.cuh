@@ -1,17 +1,20 @@
 // Two-buffer step with Phi at the current level, FP32 periodic lattices:
-// persistent CTAs whose tiles (32 x 8 nodes) arrive in shared memory by TMA.
+// persistent CTAs whose tiles (32 x TMA_TH nodes) arrive in shared memory by
+// TMA.
 //
 // Each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it
-// works on one tile, the tensor-memory accelerator copies the next tile's box
-// (the 9 population planes of x0-4 .. x0+35 by y0-1 .. y0+8: the tile, its
-// one-node halo, and the columns that keep the box's x origin on a 16-byte
-// boundary) into the other of two shared-memory stages, completing on an
-// mbarrier.  Phase 1 takes Phi of the tile and its halo from the stage (a
-// halo cell across the lattice edge, which the box fills with zeros, is read
-// at its periodic image from global memory); phase 2 collides and pushes f*
-// to the other buffer as k_step_ab<S, false> does.  Every wait on an mbarrier
-// is bounded: past `wait_limit` polls the CTA records the failure in *err,
-// waits (bounded by TMA_WAIT_LIMIT) for its own copies in flight and returns.
+// works on one tile, the tensor-memory accelerator copies the boxes of the
+// next TMA_STAGES - 1 tiles (the 9 population planes of x0-4 .. x0+35 by
+// y0-1 .. y0+TMA_TH: the tile, its one-node halo, and the columns that keep
+// the box's x origin on a 16-byte boundary) into the other shared-memory
+// stages, each completing on its own mbarrier.  A thread owns the nodes of
+// its column in rows ty, ty + 8, ...  Phase 1 takes Phi of the tile and its
+// halo from the stage (a halo cell across the lattice edge, which the box
+// fills with zeros, is read at its periodic image from global memory); phase
+// 2 collides and pushes f* to the other buffer as k_step_ab<S, false> does.
+// Every wait on an mbarrier is bounded: past `wait_limit` polls the CTA
+// records the failure in *err, waits (bounded by TMA_WAIT_LIMIT) for its own
+// copies in flight and returns.
 #pragma once
 #include <cuda.h>
 
@@ -21,6 +24,8 @@
 namespace trt {
 
 constexpr unsigned TMA_STAGE_BYTES = 9u * TMA_BY * TMA_BX * 4u;
+constexpr int TMA_R = TMA_TH / AB_TY;   // nodes per thread
+static_assert(TMA_TH % AB_TY == 0 && TMA_STAGES >= 2, "tile height and stage count");
 constexpr long long TMA_WAIT_LIMIT = kDefaultWaitLimit;
 
 // One stage; padded so that both stages start on a 128-byte boundary.
@@ -97,111 +102,135 @@ __device__ __forceinline__ void tma_phi_smem(const Args<float>& a, const TmaStag
     py = rho * uy * uy * uy;
 }
 
+// Shared memory of k_step_ab_tma (dynamic; its start is rounded up to 128 B).
+struct TmaSmem {
+    TmaStage stage[TMA_STAGES];
+    float sx[TMA_TH][AB_TX + 2];     // Phi_xxx of the tile rows, with the left/right halo
+    float sy[TMA_TH + 2][AB_TX];     // Phi_yyy of the tile columns, with the bottom/top halo
+    unsigned long long bar[TMA_STAGES];
+};
+constexpr size_t TMA_SMEM_BYTES = sizeof(TmaSmem) + 128;
+
+__device__ __forceinline__ void tma_issue(TmaSmem& sm, int k, const CUtensorMap* map, int tile,
+                                          int tiles_x) {
+    mbar_expect_tx(&sm.bar[k], TMA_STAGE_BYTES);
+    tma_load_box(&sm.stage[k], map, (tile % tiles_x) * AB_TX - TMA_XOFF, (tile / tiles_x) * TMA_TH - 1,
+                 &sm.bar[k]);
+}
+
 template <typename S>
-__global__ void __launch_bounds__(AB_TX * AB_TY, 4)
+__global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 4 : 3)
     k_step_ab_tma(const __grid_constant__ CUtensorMap tmap, Args<float> a, float* __restrict__ dst,
                   int tiles_x, int ntiles, int* __restrict__ err, long long wait_limit) {
     static_assert(sizeof(S) == 4, "FP32 storage only");
-    __shared__ __align__(128) TmaStage stage[2];
-    __shared__ float sx[AB_TY][AB_TX + 2];
-    __shared__ float sy[AB_TY + 2][AB_TX];
-    __shared__ __align__(8) unsigned long long bar[2];
+    extern __shared__ unsigned char tma_smem_raw[];
+    TmaSmem& sm = *reinterpret_cast<TmaSmem*>(tma_smem_raw + ((128u - (smem_u32(tma_smem_raw) & 127u)) & 127u));
     const float* __restrict__ F = static_cast<const float*>(a.f);
     const int tid = (int)threadIdx.x, tx = tid % AB_TX, ty = tid / AB_TX;
+    const int grid = (int)gridDim.x;
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(&sm.bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     int tile = (int)blockIdx.x;
-    if (tid == 0 && tile < ntiles) {
-        mbar_expect_tx(&bar[0], TMA_STAGE_BYTES);
-        tma_load_box(&stage[0], &tmap, (tile % tiles_x) * AB_TX - TMA_XOFF, (tile / tiles_x) * AB_TY - 1,
-                     &bar[0]);
-    }
-    unsigned phase0 = 0u, phase1 = 0u;   // parity of the next completion of bar[0] / bar[1]
-    for (int j = 0; tile < ntiles; ++j, tile += (int)gridDim.x) {
-        const int s = j & 1;
-        const int next = tile + (int)gridDim.x;
-        if (tid == 0 && next < ntiles) {
-            // the other stage was last read before the previous iteration's
-            // closing barrier; order those reads before the async write
+    if (tid == 0)
+        for (int k = 0; k < TMA_STAGES - 1; ++k)
+            if (tile + k * grid < ntiles) tma_issue(sm, k, &tmap, tile + k * grid, tiles_x);
+    unsigned phases = 0u;   // bit k: parity of the next completion of bar[k]
+    for (int s = 0; tile < ntiles; tile += grid, s = s + 1 == TMA_STAGES ? 0 : s + 1) {
+        const int ahead = tile + (TMA_STAGES - 1) * grid;
+        const int sa = s == 0 ? TMA_STAGES - 1 : s - 1;   // stage of the tile `ahead`
+        if (tid == 0 && ahead < ntiles) {
+            // stage sa was last read before the previous iteration's closing
+            // barrier; order those reads before the async write
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[s ^ 1], TMA_STAGE_BYTES);
-            tma_load_box(&stage[s ^ 1], &tmap, (next % tiles_x) * AB_TX - TMA_XOFF,
-                         (next / tiles_x) * AB_TY - 1, &bar[s ^ 1]);
+            tma_issue(sm, sa, &tmap, ahead, tiles_x);
         }
-        const unsigned ph = s ? phase1 : phase0;
-        const bool ok = mbar_wait(&bar[s], ph, wait_limit);
-        if (s) phase1 ^= 1u;
-        else phase0 ^= 1u;
+        const unsigned ph = (phases >> s) & 1u;
+        const bool ok = mbar_wait(&sm.bar[s], ph, wait_limit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 if (err) atomicExch(err, 1);
-                mbar_wait(&bar[s], ph);                                          // the late copy
-                if (next < ntiles) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1);   // the next one
+                // the copies in flight: this tile's and those of the next
+                // TMA_STAGES - 1 tiles
+                for (int k = 0; k < TMA_STAGES; ++k) {
+                    const int sk = (s + k) % TMA_STAGES;
+                    if (tile + k * grid < ntiles) mbar_wait(&sm.bar[sk], (phases >> sk) & 1u);
+                }
             }
             return;
         }
-        const TmaStage& st = stage[s];
-        const int x0 = (tile % tiles_x) * AB_TX, y0 = (tile / tiles_x) * AB_TY;
-        const int x = x0 + tx, y = y0 + ty;
-        const bool inside = x < a.nx && y < a.ny;
+        phases ^= 1u << s;
+        const TmaStage& st = sm.stage[s];
+        const int x0 = (tile % tiles_x) * AB_TX, y0 = (tile / tiles_x) * TMA_TH;
+        const int x = x0 + tx;
 
-        // phase 1: Phi of the tile and its halo
-        float d[9];
+        // phase 1: Phi of the tile and its halo; the tile nodes keep their
+        // moments for the collision
+        NodeMom<float> m[TMA_R];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = st.v[i][ty + 1][tx + TMA_XOFF];
-        float px = 0.f, py = 0.f;
-        if (inside) {
-            float rho, ux, uy;
-            moments_of<float>(d, a.gx, a.gy, a.rho0, rho, ux, uy);
-            px = rho * ux * ux * ux;
-            py = rho * uy * uy * uy;
-        } else if ((x == a.nx && y < a.ny) || (y == a.ny && x < a.nx)) {
-            tma_phi_global(a, F, ab_wrap(x, a.nx), ab_wrap(y, a.ny), px, py);
+        for (int r = 0; r < TMA_R; ++r) {
+            const int ry = ty + r * AB_TY, y = y0 + ry;
+            float d[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = st.v[i][ry + 1][tx + TMA_XOFF];
+            m[r] = node_moments<float>(d, a.gx, a.gy, a.rho0);
+            float px = 0.f, py = 0.f;
+            if (x < a.nx && y < a.ny) {
+                px = m[r].rho * m[r].ux * m[r].ux * m[r].ux;
+                py = m[r].rho * m[r].uy * m[r].uy * m[r].uy;
+            } else if ((x == a.nx && y < a.ny) || (y == a.ny && x < a.nx)) {
+                tma_phi_global(a, F, ab_wrap(x, a.nx), ab_wrap(y, a.ny), px, py);
+            }
+            sm.sx[ry][tx + 1] = px;
+            sm.sy[ry + 1][tx] = py;
         }
-        sx[ty][tx + 1] = px;
-        sy[ty + 1][tx] = py;
-        if (tid < 2 * AB_TY) {                          // left / right halo columns
-            const int r = tid % AB_TY, side = tid / AB_TY;
+        if (tid < 2 * TMA_TH) {                          // left / right halo columns
+            const int r = tid % TMA_TH, side = tid / TMA_TH;
             const int hx = side ? x0 + AB_TX : x0 - 1, hy = y0 + r;
             float qx = 0.f, qy = 0.f;
             if (hy < a.ny && (side ? x0 + AB_TX - 1 < a.nx : true)) {
                 if (hx >= 0 && hx < a.nx) tma_phi_smem(a, st, hx - x0 + TMA_XOFF, r + 1, qx, qy);
                 else tma_phi_global(a, F, ab_wrap(hx, a.nx), hy, qx, qy);
             }
-            sx[r][side ? AB_TX + 1 : 0] = qx;
-        } else if (tid < 2 * AB_TY + 2 * AB_TX) {       // bottom / top halo rows
-            const int k = tid - 2 * AB_TY;
+            sm.sx[r][side ? AB_TX + 1 : 0] = qx;
+        } else if (tid < 2 * TMA_TH + 2 * AB_TX) {       // bottom / top halo rows
+            const int k = tid - 2 * TMA_TH;
             const int c = k % AB_TX, side = k / AB_TX;
-            const int hx = x0 + c, hy = side ? y0 + AB_TY : y0 - 1;
+            const int hx = x0 + c, hy = side ? y0 + TMA_TH : y0 - 1;
             float qx = 0.f, qy = 0.f;
-            if (hx < a.nx && (side ? y0 + AB_TY - 1 < a.ny : true)) {
-                if (hy >= 0 && hy < a.ny) tma_phi_smem(a, st, c + TMA_XOFF, side ? AB_TY + 1 : 0, qx, qy);
+            if (hx < a.nx && (side ? y0 + TMA_TH - 1 < a.ny : true)) {
+                if (hy >= 0 && hy < a.ny) tma_phi_smem(a, st, c + TMA_XOFF, side ? TMA_TH + 1 : 0, qx, qy);
                 else tma_phi_global(a, F, hx, ab_wrap(hy, a.ny), qx, qy);
             }
-            sy[side ? AB_TY + 1 : 0][c] = qy;
+            sm.sy[side ? TMA_TH + 1 : 0][c] = qy;
         }
         __syncthreads();
 
         // phase 2: collide and push
-        if (inside) {
-            const float dpx = 0.5f * (sx[ty][tx + 2] - sx[ty][tx]);
-            const float dpy = 0.5f * (sy[ty + 2][tx] - sy[ty][tx]);
-            float o[9], phx, phy;
-            collide<float>(d, dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
-            const int xm = ab_wrap(x - 1, a.nx), xp = ab_wrap(x + 1, a.nx);
-            const long long rm = (long long)ab_wrap(y - 1, a.ny) * a.pitch;
-            const long long r0 = (long long)y * a.pitch;
-            const long long rp = (long long)ab_wrap(y + 1, a.ny) * a.pitch;
+        const int xm = ab_wrap(x - 1, a.nx), xp = ab_wrap(x + 1, a.nx);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const long long row = ey(i) > 0 ? rp : (ey(i) < 0 ? rm : r0);
-                const int col = ex(i) > 0 ? xp : (ex(i) < 0 ? xm : x);
-                dst[(long long)i * a.plane + row + col] = o[i];
+        for (int r = 0; r < TMA_R; ++r) {
+            const int ry = ty + r * AB_TY, y = y0 + ry;
+            if (x < a.nx && y < a.ny) {
+                const float dpx = 0.5f * (sm.sx[ry][tx + 2] - sm.sx[ry][tx]);
+                const float dpy = 0.5f * (sm.sy[ry + 2][tx] - sm.sy[ry][tx]);
+                float o[9], phx, phy;
+                collide_from<float>(m[r], dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, o, phx,
+                                    phy);
+                // in-plane offsets in 32 bits (a plane holds fewer than 2^31 nodes)
+                const int rm = ab_wrap(y - 1, a.ny) * a.pitch;
+                const int r0 = y * a.pitch;
+                const int rp = ab_wrap(y + 1, a.ny) * a.pitch;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int row = ey(i) > 0 ? rp : (ey(i) < 0 ? rm : r0);
+                    const int col = ex(i) > 0 ? xp : (ex(i) < 0 ? xm : x);
+                    float* __restrict__ q = dst + (long long)i * a.plane;
+                    q[row + col] = o[i];
+                }
             }
         }
         __syncthreads();   // sx, sy and this stage are free again

@@ -276,32 +276,46 @@ __device__ __forceinline__ void collide_dw(const df64 (&d)[9], df64 dpx, df64 dp
     phy = ruyy * uy;
 }
 
+// Raw moments of one node's shifted populations and its eq11 velocity: the
+// first half of the collision, which the two-buffer TMA kernel also uses for
+// Phi before its halo barrier.
+template <typename C> struct NodeMom {
+    C drho, s13, s24, sd, pxy, qxxy, qxyy, jx, jy;   // sums of d weighted by e
+    C rho, ux, uy;
+};
+
 template <typename C>
-__device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k1lo,
-                                        const C k2, const C k2lo, const C kf, const C gx,
-                                        const C gy, const C rho0, C (&o)[9], C& phx, C& phy) {
-    if constexpr (std::is_same<C, df64>::value) {
-        collide_dw(d, dpx, dpy, k1, k2, kf, gx, gy, rho0, o, phx, phy);
-        return;
-    } else {
-    const C third = C(1.0 / 3.0);
-    // raw moments of the shifted populations
-    const C s13 = d[1] + d[3], m13 = d[1] - d[3];
-    const C s24 = d[2] + d[4], m24 = d[2] - d[4];
+__device__ __forceinline__ NodeMom<C> node_moments(const C (&d)[9], const C gx, const C gy,
+                                                   const C rho0) {
+    NodeMom<C> m;
+    m.s13 = d[1] + d[3];
+    const C m13 = d[1] - d[3];
+    m.s24 = d[2] + d[4];
+    const C m24 = d[2] - d[4];
     const C a57 = d[5] + d[7], m57 = d[5] - d[7];
     const C a68 = d[6] + d[8], m68 = d[6] - d[8];
-    const C sd = a57 + a68;      // sum of the four diagonal populations
-    const C pxy = a57 - a68;     // sum e_x e_y d
-    const C qxxy = m57 + m68;    // sum e_x^2 e_y d
-    const C qxyy = m57 - m68;    // sum e_x e_y^2 d
-    const C jx = m13 + qxyy;     // sum e_x d
-    const C jy = m24 + qxxy;     // sum e_y d
-    const C drho = (d[0] + sd) + (s13 + s24);
+    m.sd = a57 + a68;      // sum of the four diagonal populations
+    m.pxy = a57 - a68;     // sum e_x e_y d
+    m.qxxy = m57 + m68;    // sum e_x^2 e_y d
+    m.qxyy = m57 - m68;    // sum e_x e_y^2 d
+    m.jx = m13 + m.qxyy;   // sum e_x d
+    m.jy = m24 + m.qxxy;   // sum e_y d
+    m.drho = (d[0] + m.sd) + (m.s13 + m.s24);
     // eq11: rho = sum f, u = (sum e f)/rho + g/2
-    const C rho = rho0 + drho;
-    const C inv = C(1) / rho;
-    const C ux = jx * inv + C(0.5) * gx;
-    const C uy = jy * inv + C(0.5) * gy;
+    m.rho = rho0 + m.drho;
+    const C inv = C(1) / m.rho;
+    m.ux = m.jx * inv + C(0.5) * gx;
+    m.uy = m.jy * inv + C(0.5) * gy;
+    return m;
+}
+
+// The rest of the collision (eq2 with eq9, eq_Gi and eq6) from the moments.
+template <typename C>
+__device__ __forceinline__ void collide_from(const NodeMom<C>& m, C dpx, C dpy, const C k1,
+                                             const C k1lo, const C k2, const C k2lo, const C kf,
+                                             const C gx, const C gy, C (&o)[9], C& phx, C& phy) {
+    const C third = C(1.0 / 3.0);
+    const C drho = m.drho, rho = m.rho, ux = m.ux, uy = m.uy, jx = m.jx, jy = m.jy;
     const C Fx = rho * gx, Fy = rho * gy;
     const C rux = rho * ux, ruy = rho * uy;
     const C ruxx = rux * ux, ruyy = ruy * uy, ruxy = rux * uy;
@@ -311,9 +325,9 @@ __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k
     // eq9_2 they are the non-equilibrium projections A of eq9 (A_x = -F_x/2
     // is folded into a1)
     const C drho3 = third * drho;
-    const C Pxx = (s13 + sd) - drho3, Pyy = (s24 + sd) - drho3;
-    const C Qxxy = qxxy - third * jy, Qxyy = qxyy - third * jx;
-    const C Axx = Pxx - ruxx, Ayy = Pyy - ruyy, Axy = pxy - ruxy;
+    const C Pxx = (m.s13 + m.sd) - drho3, Pyy = (m.s24 + m.sd) - drho3;
+    const C Qxxy = m.qxxy - third * jy, Qxyy = m.qxyy - third * jx;
+    const C Axx = Pxx - ruxx, Ayy = Pyy - ruyy, Axy = m.pxy - ruxy;
     const C Axxy = Qxxy - rxxy, Axyy = Qxyy - rxyy;
     // relaxation: (1 - 1/tau) A with 1 - 1/tau carried as hi + lo, so the rate
     // 1/tau stays exact to ~2^-48 even when tau is large (FP32 alone would
@@ -357,6 +371,17 @@ __device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k
     o[8] = c68 - o68;
     phx = ruxx * ux;
     phy = ruyy * uy;
+}
+
+template <typename C>
+__device__ __forceinline__ void collide(const C (&d)[9], C dpx, C dpy, const C k1, const C k1lo,
+                                        const C k2, const C k2lo, const C kf, const C gx,
+                                        const C gy, const C rho0, C (&o)[9], C& phx, C& phy) {
+    if constexpr (std::is_same<C, df64>::value) {
+        collide_dw(d, dpx, dpy, k1, k2, kf, gx, gy, rho0, o, phx, phy);
+    } else {
+        collide_from<C>(node_moments<C>(d, gx, gy, rho0), dpx, dpy, k1, k1lo, k2, k2lo, kf, gx, gy, o,
+                        phx, phy);
     }
 }
 

@@ -21,9 +21,12 @@ constexpr int VEC16_NODES = 4;
 inline int vec_width(int storage_bytes) { return storage_bytes == 2 ? VEC16_NODES : 16 / storage_bytes; }
 
 // Format-independent description of a lattice's device state.
-// Box of the TMA-fed two-buffer kernel (lb_ab_tma.cuh): x0-4 .. x0+35 by
-// y0-1 .. y0+8 around a 32 x 8 tile, all 9 population planes.
-constexpr int TMA_BX = 40, TMA_BY = 10, TMA_XOFF = 4;
+// TMA-fed two-buffer kernel (lb_ab_tma.cuh): a tile of 32 x TMA_TH nodes, a
+// thread owning TMA_TH / 8 of them (one per 8 rows), and its box x0-4 .. x0+35
+// by y0-1 .. y0+TMA_TH, all 9 population planes, in one of TMA_STAGES
+// shared-memory stages.
+constexpr int TMA_TH = 8, TMA_STAGES = 2;
+constexpr int TMA_BX = 40, TMA_BY = TMA_TH + 2, TMA_XOFF = 4;
 // Polls of an mbarrier before a kernel's wait gives up (microseconds suffice
 // for a tile copy; the limit only bounds a wait that would never end).
 constexpr long long kDefaultWaitLimit = 1ll << 22;

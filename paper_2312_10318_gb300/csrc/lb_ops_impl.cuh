@@ -81,10 +81,10 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
         if (!s.general && s.tma_grid > 0 && s.kerr) {
             const int k = v.f == s.tma_buf[0] ? 0 : 1;
             const CUtensorMap* map = static_cast<const CUtensorMap*>(s.tma_map[k]);
-            const int ntiles = (int)(g.x * g.y);
+            const int ntiles = (int)g.x * ((s.ny + TMA_TH - 1) / TMA_TH);
             const int grid = ntiles < s.tma_grid ? ntiles : s.tma_grid;
-            k_step_ab_tma<S><<<grid, AB_TX * AB_TY, 0, st>>>(*map, a, static_cast<S*>(v.f2), (int)g.x,
-                                                             ntiles, s.kerr, s.wait_limit);
+            k_step_ab_tma<S><<<grid, AB_TX * AB_TY, TMA_SMEM_BYTES, st>>>(
+                *map, a, static_cast<S*>(v.f2), (int)g.x, ntiles, s.kerr, s.wait_limit);
             return cudaGetLastError();
         }
     }
@@ -99,8 +99,15 @@ int Ops<S>::tma_grid() {
         int dev = 0, sms = 0, occ = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_ab_tma<S>, AB_TX * AB_TY, 0) !=
-                cudaSuccess)
+            cudaFuncSetAttribute(k_step_ab_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TMA_SMEM_BYTES) != cudaSuccess ||
+            // all of the unified L1/shared array as shared memory, so that the
+            // resident CTAs the occupancy query counts are the ones that run
+            // (the grid is persistent: one missing CTA per SM is a second wave)
+            cudaFuncSetAttribute(k_step_ab_tma<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_ab_tma<S>, AB_TX * AB_TY,
+                                                          TMA_SMEM_BYTES) != cudaSuccess)
             return 0;
         return occ * sms;
     } else {

@@ -121,9 +121,9 @@ cudaError_t ensure_stage(trtrlb_lattice* h) {
 
 // TMA descriptor of one FP32 population buffer for k_step_ab_tma: a 3-D tensor
 // (x: nx, y: ny rows of `pitch` floats, plane: 9 planes of ny * pitch floats)
-// read in boxes of 40 x 10 x 9 (the 32 x 8 tile, its one-node halo and the
-// columns that keep the box origin 16-byte aligned); outside the lattice the
-// box is filled with zeros.
+// read in boxes of 40 x (TMA_TH + 2) x 9 (the 32 x TMA_TH tile, its one-node
+// halo and the columns that keep the box origin 16-byte aligned); outside the
+// lattice the box is filled with zeros.
 cudaError_t encode_tma(void* base, int nx, int ny, int pitch, CUtensorMap* out) {
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,

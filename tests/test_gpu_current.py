@@ -96,7 +96,9 @@ def test_lag_of_phi_is_a_higher_order_effect(gpu_lib):
     assert lag < 1e-2 * err
 
 
-@pytest.mark.parametrize("storage,bound", [("f32", 3e-5), ("f16", 1.5e-2), ("bf16", 2e-1)])
+# the Taylor-Green bounds of the in-place kernels (FP32: 1e-4, the worst-case
+# linear growth of the storage rounding over 1000 steps; measured 3.0e-5)
+@pytest.mark.parametrize("storage,bound", [("f32", 1e-4), ("f16", 1.5e-2), ("bf16", 2e-1)])
 @pytest.mark.parametrize("n", [64, 67])
 def test_current_phi_reduced_precision_taylor_green(gpu_lib, storage, bound, n):
     """The two-buffer kernel in FP32 / FP16 / BF16 storage (periodic path, full
