@@ -109,6 +109,11 @@ def alu_roofline(storage: str, nodes_per_launch: float, launch_s: float):
             "traffic": None, "ops_per_node": FP64_OPS_PER_NODE}
 
 
+# GB300's nominal HBM3e bandwidth; the line reports its fraction beside the
+# measured copy bandwidth's (the roofline's denominator).
+HBM_NOMINAL_GBS = 7900.0
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -547,6 +552,7 @@ def main():
         line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0])
         line["roofline"]["launch_ms"] = launch_s * 1e3
         line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
+        line["roofline"]["frac_of_nominal_hbm"] = achieved / HBM_NOMINAL_GBS
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(problems)
         if not args.no_serve:
