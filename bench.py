@@ -125,12 +125,17 @@ def hbm_peak():
 
 def kernel_source_hash() -> str:
     """Hash of the device-code sources (headers with the kernels and their
-    launch code, and the per-format instantiation units)."""
+    launch code, and the per-format instantiation units) with comments and
+    blank lines removed, so that only a change of code invalidates a capture."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_10318_gb300", "csrc")
     for p in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "lb_ops_*.cu"))):
-        with open(p, "rb") as fh:
-            h.update(fh.read())
+        with open(p, encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = re.sub(r"//.*", "", line).rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

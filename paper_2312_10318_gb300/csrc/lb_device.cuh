@@ -402,11 +402,14 @@ __device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, 
 
 // Resident 256-thread CTAs per SM the scalar step kernels ask the compiler to
 // allow: the FP32 periodic step with lagged G fits 40 registers without
-// spilling (6 CTAs, 75 % occupancy for the odd step instead of 5); the other
-// variants keep the compiler's choice.
+// spilling (6 CTAs, 75 % occupancy for the odd step instead of 5), the
+// periodic double-word step 64 (4 CTAs; the odd step took 79 and 3); the
+// other variants keep the compiler's choice.
 template <typename S, bool GENERAL, int GMODE>
 __host__ __device__ constexpr int step_min_blocks() {
-    return (sizeof(S) == 4 && !GENERAL && GMODE == G_LAGGED) ? 6 : 1;
+    return (sizeof(S) == 4 && !GENERAL && GMODE == G_LAGGED) ? 6
+           : (std::is_same<S, f64dw>::value && !GENERAL)          ? 4
+                                                                   : 1;
 }
 
 // One fused AA step of one node (pull-stream, moments, regularized TRT
