@@ -123,12 +123,12 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(csrc: str | None = None) -> str:
     """Hash of the device-code sources (headers with the kernels and their
     launch code, and the per-format instantiation units) with comments and
     blank lines removed, so that only a change of code invalidates a capture."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2312_10318_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2312_10318_gb300", "csrc")
     for p in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "lb_ops_*.cu"))):
         with open(p, encoding="utf-8") as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)

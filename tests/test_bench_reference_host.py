@@ -28,3 +28,22 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+
+
+def test_source_hash_ignores_comments_but_not_code(tmp_path):
+    """The recorded DRAM traffic stays valid across comment edits and is
+    dropped when the device code changes."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2312_10318_gb300", "csrc")
+    dst = tmp_path / "csrc"
+    shutil.copytree(src, dst)
+    h0 = bench.kernel_source_hash(str(dst))
+    assert h0 == bench.kernel_source_hash()
+    p = dst / "lb_batch.cuh"
+    text = p.read_text()
+    p.write_text("// a new comment line\n\n" + text.replace("namespace trt {", "namespace trt {  /* note */", 1))
+    assert bench.kernel_source_hash(str(dst)) == h0
+    p.write_text(text.replace("BATCH_THREADS = 256", "BATCH_THREADS = 128", 1))
+    assert bench.kernel_source_hash(str(dst)) != h0
