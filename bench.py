@@ -250,14 +250,48 @@ def cpu_baseline(problems, seconds: float = 12.0):
                              wall_rho=pr.wall_rho), mask=pr.mask)
     lat.init(pr.ux, pr.uy, pr.rho)
     lat.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        lat.step(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": pr.nodes * n / dt / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+
+    def rate(budget):
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            lat.step(1)
+            n += 1
+        return n, time.perf_counter() - t0
+
+    n, dt = rate(seconds)
+    cores = O.num_threads()
+    # the same sample on one core, then the thread count restored
+    O.set_num_threads(1)
+    try:
+        n1, dt1 = rate(seconds / 3)
+    finally:
+        O.set_num_threads(cores)
+    return {"value": pr.nodes * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} time steps of one {pr.nx}x{pr.ny} lattice ({pr.name}) of the workload, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "one_core": {"value": pr.nodes * n1 / dt1 / 1e6, "unit": UNIT,
+                         "sample": f"{n1} time steps of the same lattice, {dt1:.1f} s"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f" ({os.cpu_count()} logical CPUs)"
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip() + f" ({os.cpu_count()} logical CPUs)"
+    except OSError:
+        pass
+    import platform
+    return f"{platform.machine()} ({os.cpu_count()} logical CPUs)"
 
 
 def run_serving(args) -> dict:
@@ -367,7 +401,7 @@ def run_reference(args, problems, desc, budget_s: float = 60.0):
             "data": "synthetic",
             "config": {"workload": desc, "nodes_per_step": nodes, "implementation": "FP64 CPU oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -88,6 +88,7 @@ def lib():
         L.orc_drag.argtypes = [P, vp, _D, _D]
         L.orc_zou_he.argtypes = [P, vp, _D]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
         _LIB = L
     return _LIB
 
@@ -249,6 +250,11 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Sets the OpenMP threads of the oracle's loops (timing on one core)."""
+    lib().orc_set_num_threads(int(n))
+
+
 def tau2_from_magic(tau1: float, magic: float) -> float:
     """tau_{s,2} from Lambda_s = (tau1 - 1/2)(tau2 - 1/2), eq_a29."""
     return 0.5 + magic / (tau1 - 0.5)
@@ -260,5 +266,5 @@ def viscosity(tau1: float) -> float:
 
 
 __all__ = ["Params", "Lattice", "lattice", "hermite", "equilibrium", "forcing", "compensation",
-           "projections", "macroscopic", "collide_node", "l2", "num_threads", "tau2_from_magic", "viscosity",
+           "projections", "macroscopic", "collide_node", "l2", "num_threads", "set_num_threads", "tau2_from_magic", "viscosity",
            "zou_he", "FLUID", "SOLID", "INLET", "OUTLET", "PRESSURE", "G_LAGGED", "G_CURRENT", "G_OFF"]

@@ -115,6 +115,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Sets the threads of the following loops (n >= 1); for timing on one core. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---- exported lattice description, for the identity tests ------------- */
 void orc_lattice(int32_t* e /* [9][2] */, double* w /* [9] */, double* cs2) {
     for (int i = 0; i < NQ; ++i) {

@@ -47,3 +47,17 @@ def test_source_hash_ignores_comments_but_not_code(tmp_path):
     assert bench.kernel_source_hash(str(dst)) == h0
     p.write_text(text.replace("BATCH_THREADS = 256", "BATCH_THREADS = 128", 1))
     assert bench.kernel_source_hash(str(dst)) != h0
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    """The oracle baseline gives its all-threads rate, a one-core rate of the
+    same lattice, the CPU model, and leaves the oracle's thread count as it was."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle as O
+    from paper_2312_10318_gb300 import workloads as W
+    before = O.num_threads()
+    cb = bench.cpu_baseline([W.double_shear_layer(64, re=1e4)], seconds=0.3)
+    assert O.num_threads() == before
+    assert cb["kind"] == "oracle" and cb["cores"] == before and cb["value"] > 0
+    assert cb["one_core"]["value"] > 0 and cb["cpu_model"]
