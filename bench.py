@@ -41,9 +41,9 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f64dw": 8}
 PHI_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4, "f64dw": 8}
 
 
-def workload(name: str, size=None, storage=None):
-    """(problems, storage, description) of a named workload; size "NXxNY" and
-    storage override the defaults (for profiling runs)."""
+def workload(name: str, size=None, storage=None, g_mode: str = "lagged"):
+    """(problems, storage, description) of a named workload; size "NXxNY",
+    storage and the G mode override the defaults (for profiling runs)."""
     from paper_2312_10318_gb300 import workloads as W
     if name == "dsl1024":
         res = (1e4, 1e5, 1e7)
@@ -54,7 +54,7 @@ def workload(name: str, size=None, storage=None):
             probs = [_rect(p, nx, ny) for p in probs]
         st = storage or "f32"
         desc = (f"double shear layer, 3 lattices {nx}x{ny} periodic (Re 1e4, 1e5, 1e7), kappa=80, "
-                f"delta=0.05, u_c=0.04, tau_s2=0.625, {st.upper()} storage, G lagged")
+                f"delta=0.05, u_c=0.04, tau_s2=0.625, {st.upper()} storage, G {g_mode}")
         return probs, st, desc
     if name == "dsl4096":
         nx, ny = (4096, 4096) if size is None else size
@@ -62,11 +62,11 @@ def workload(name: str, size=None, storage=None):
         if size is not None:
             p = _rect(p, nx, ny)
         st = storage or "f32"
-        return [p], st, f"double shear layer, 1 lattice {nx}x{ny} periodic, Re 1e5, {st.upper()} storage, G lagged"
+        return [p], st, f"double shear layer, 1 lattice {nx}x{ny} periodic, Re 1e5, {st.upper()} storage, G {g_mode}"
     if name == "tg64":
         probs = [W.taylor_green(64, 0.04, 100.0, magic=0.25)]
         st = storage or "f64"
-        return probs, st, f"Taylor-Green 64x64 periodic, u0=0.04, Re=100, magic 1/4, {st.upper()}"
+        return probs, st, f"Taylor-Green 64x64 periodic, u0=0.04, Re=100, magic 1/4, {st.upper()}, G {g_mode}"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -445,7 +445,7 @@ def main():
     if args.size:
         nx_s, ny_s = args.size.lower().split("x")
         size = (int(nx_s), int(ny_s))
-    problems, storage, desc = workload(args.workload, size, args.storage)
+    problems, storage, desc = workload(args.workload, size, args.storage, args.g_mode)
     if args.impl == "reference":
         return run_reference(args, problems, desc)
 
