@@ -239,7 +239,13 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
-def cpu_baseline(problems, seconds: float = 12.0):
+def oracle_g_mode(g_mode: str) -> int:
+    """The oracle's code of a G mode name (lagged, current, off)."""
+    import oracle as O
+    return {"lagged": O.G_LAGGED, "current": O.G_CURRENT, "off": O.G_OFF}[g_mode]
+
+
+def cpu_baseline(problems, seconds: float = 12.0, g_mode: str = "lagged"):
     """The FP64 CPU oracle on a bounded sample of the workload: as many time steps
     of the first lattice as fit in about `seconds`."""
     import oracle as O
@@ -247,7 +253,7 @@ def cpu_baseline(problems, seconds: float = 12.0):
     lat = O.Lattice(O.Params(nx=pr.nx, ny=pr.ny, tau1=pr.tau_s, tau2=pr.tau_s2,
                              periodic_x=pr.periodic[0], periodic_y=pr.periodic[1],
                              gx=pr.g[0], gy=pr.g[1], wall_ux=pr.wall_u[0], wall_uy=pr.wall_u[1],
-                             wall_rho=pr.wall_rho), mask=pr.mask)
+                             wall_rho=pr.wall_rho, g_mode=oracle_g_mode(g_mode)), mask=pr.mask)
     lat.init(pr.ux, pr.uy, pr.rho)
     lat.step(1)
 
@@ -369,7 +375,7 @@ def run_reference(args, problems, desc, budget_s: float = 60.0):
         lat = O.Lattice(O.Params(nx=pr.nx, ny=rows, tau1=pr.tau_s, tau2=pr.tau_s2,
                                  periodic_x=pr.periodic[0], periodic_y=pr.periodic[1] or rows < pr.ny,
                                  gx=pr.g[0], gy=pr.g[1], wall_ux=pr.wall_u[0], wall_uy=pr.wall_u[1],
-                                 wall_rho=pr.wall_rho),
+                                 wall_rho=pr.wall_rho, g_mode=oracle_g_mode(args.g_mode)),
                         mask=None if pr.mask is None else pr.mask[:rows])
         rho = None if pr.rho is None else pr.rho[:rows]
         return lat.init(pr.ux[:rows], pr.uy[:rows], rho)
@@ -593,7 +599,7 @@ def main():
         line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
         line["roofline"]["frac_of_nominal_hbm"] = achieved / HBM_NOMINAL_GBS
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(problems)
+            line["cpu_baseline"] = cpu_baseline(problems, g_mode=args.g_mode)
         if not args.no_serve:
             line["serving"] = run_serving(args)
         print(json.dumps(line), flush=True)
