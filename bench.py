@@ -139,9 +139,18 @@ def kernel_source_hash(csrc: str | None = None) -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_label(args, vector: bool) -> str:
+def tma_grouped(args, storage: str, problems) -> bool:
+    """Whether a batch step of G_CURRENT lattices is one TMA-fed launch for all
+    of them (FP32, periodic, no mask, at most 16 lattices)."""
+    return (args.mode == "batch" and args.g_mode == "current" and storage == "f32" and len(problems) <= 16
+            and all(p.mask is None and all(p.periodic) for p in problems))
+
+
+def kernel_label(args, vector: bool, grouped: bool = False) -> str:
     """Name of the step kernel the timed region launches."""
     if args.g_mode == "current":
+        if grouped:
+            return "trt::k_step_ab_tma (two-buffer step, Phi at the current level, all lattices in one launch)"
         return "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)"
     if args.mode == "batch":
         return ("trt::k_step_group_vec" if vector else "trt::k_step_group") + \
@@ -536,7 +545,8 @@ def main():
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
     # the two-buffer (current-Phi) kernel runs one launch per lattice in a batch
-    per_step_launches = 1 if (args.mode == "batch" and args.g_mode != "current") else len(lats)
+    grouped = tma_grouped(args, storage, problems)
+    per_step_launches = 1 if (args.mode == "batch" and (args.g_mode != "current" or grouped)) else len(lats)
     launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
     per_launch_bytes = bytes_per_node(storage, args.g_mode) * nodes / per_step_launches
@@ -594,7 +604,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
         }
-        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0])
+        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0], grouped)
         line["roofline"]["launch_ms"] = launch_s * 1e3
         line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
         line["roofline"]["frac_of_nominal_hbm"] = achieved / HBM_NOMINAL_GBS

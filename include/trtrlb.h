@@ -280,7 +280,11 @@ const char* trtrlb_slabs_last_error(trtrlb_slabs_t s);
  * A batch advances several lattices together: per time step one kernel launch
  * per storage format covers every tile of every lattice in the batch (the
  * same per-node update as trtrlb_step, so results are those of stepping each
- * lattice alone).  Runs of 32 or more steps replay a captured CUDA graph when
+ * lattice alone).  G_CURRENT members take the two-buffer kernel: FP32 periodic
+ * ones without a mask share its TMA-fed launches (up to 16 lattices each; the
+ * results equal the single-lattice launch's up to the compiler's FMA
+ * contraction, a few FP32 ulps), the others take one launch each.  Runs of 32
+ * or more steps replay a captured CUDA graph when
  * the batch's stream is not the legacy default stream.  Lattices keep their
  * own parity and step count; all of them must live on the batch's device and
  * their other work must be ordered with the batch's stream by the caller

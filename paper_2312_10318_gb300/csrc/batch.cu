@@ -105,8 +105,20 @@ cudaError_t launch_steps(trtrlb_batch* b, int64_t n) {
                                            std::get<2>(k), b->stream));
             if (e != cudaSuccess) return e;
         }
+        // two-buffer (G_CURRENT) members: the TMA-fed ones share launches,
+        // the others run one launch each
+        std::vector<const trt::State*> tma;
+        for (trtrlb_lattice* h : b->lats)
+            if (h->s.g_mode == TRTRLB_G_CURRENT && h->p.storage == TRTRLB_F32 &&
+                trt::Ops<float>::tma_eligible(h->s))
+                tma.push_back(&h->s);
+        if (!tma.empty()) {
+            const cudaError_t e = trt::Ops<float>::step_ab_group(tma.data(), (int)tma.size(), flip, b->stream);
+            if (e != cudaSuccess) return e;
+        }
         for (trtrlb_lattice* h : b->lats) {
             if (h->s.g_mode == TRTRLB_G_CURRENT) {
+                if (h->p.storage == TRTRLB_F32 && trt::Ops<float>::tma_eligible(h->s)) continue;
                 const cudaError_t e = TRT_DISPATCH_S(h->p.storage, step_ab(h->s, flip, b->stream));
                 if (e != cudaSuccess) return e;
                 continue;

@@ -12,9 +12,12 @@
 // halo from the stage (a halo cell across the lattice edge, which the box
 // fills with zeros, is read at its periodic image from global memory); phase
 // 2 collides and pushes f* to the other buffer as k_step_ab<S, false> does.
+// One launch may advance several lattices (TmaGroup): their tiles are
+// numbered one lattice after the other and each tile finds its lattice by a
+// binary search over the prefix sums.
 // Every wait on an mbarrier is bounded: past `wait_limit` polls the CTA
-// records the failure in *err, waits (bounded by TMA_WAIT_LIMIT) for its own
-// copies in flight and returns.
+// records the failure in the error flag of every lattice of the launch, waits
+// (bounded by TMA_WAIT_LIMIT) for its own copies in flight and returns.
 #pragma once
 #include <cuda.h>
 
@@ -111,21 +114,46 @@ struct TmaSmem {
 };
 constexpr size_t TMA_SMEM_BYTES = sizeof(TmaSmem) + 128;
 
-__device__ __forceinline__ void tma_issue(TmaSmem& sm, int k, const CUtensorMap* map, int tile,
-                                          int tiles_x) {
-    mbar_expect_tx(&sm.bar[k], TMA_STAGE_BYTES);
-    tma_load_box(&sm.stage[k], map, (tile % tiles_x) * AB_TX - TMA_XOFF, (tile / tiles_x) * TMA_TH - 1,
-                 &sm.bar[k]);
+// The lattices of one launch (one for a single lattice, up to
+// TMA_GROUP_MAX for a batch): descriptors of the buffers they read, their
+// arguments, the buffers they write, their error flags, and the prefix sums of
+// their tiles (tiles are numbered lattice after lattice).
+constexpr int TMA_GROUP_MAX = 16;
+template <int MAXL> struct TmaGroup {
+    CUtensorMap map[MAXL];
+    Args<float> a[MAXL];
+    float* dst[MAXL];
+    int* err[MAXL];
+    int tile_begin[MAXL + 1];
+    int tiles_x[MAXL];
+    int n;
+};
+
+// Lattice of global tile `tile` (binary search over the prefix sums).
+template <int MAXL>
+__device__ __forceinline__ int tma_lattice(const TmaGroup<MAXL>& p, int tile) {
+    if constexpr (MAXL == 1) return 0;   // a single lattice: its arguments at fixed offsets
+    int lo = 0, hi = p.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tile_begin[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 4 : 3)
-    k_step_ab_tma(const __grid_constant__ CUtensorMap tmap, Args<float> a, float* __restrict__ dst,
-                  int tiles_x, int ntiles, int* __restrict__ err, long long wait_limit) {
-    static_assert(sizeof(S) == 4, "FP32 storage only");
+template <int MAXL>
+__device__ __forceinline__ void tma_issue(TmaSmem& sm, int k, const TmaGroup<MAXL>& p, int tile) {
+    const int l = tma_lattice(p, tile), t = tile - p.tile_begin[l], tw = p.tiles_x[l];
+    mbar_expect_tx(&sm.bar[k], TMA_STAGE_BYTES);
+    tma_load_box(&sm.stage[k], &p.map[l], (t % tw) * AB_TX - TMA_XOFF, (t / tw) * TMA_TH - 1, &sm.bar[k]);
+}
+
+template <int MAXL>
+__global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 5 : 3)
+    k_step_ab_tma(const __grid_constant__ TmaGroup<MAXL> p, int ntiles, long long wait_limit) {
     extern __shared__ unsigned char tma_smem_raw[];
     TmaSmem& sm = *reinterpret_cast<TmaSmem*>(tma_smem_raw + ((128u - (smem_u32(tma_smem_raw) & 127u)) & 127u));
-    const float* __restrict__ F = static_cast<const float*>(a.f);
     const int tid = (int)threadIdx.x, tx = tid % AB_TX, ty = tid / AB_TX;
     const int grid = (int)gridDim.x;
 
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 4 : 3)
     int tile = (int)blockIdx.x;
     if (tid == 0)
         for (int k = 0; k < TMA_STAGES - 1; ++k)
-            if (tile + k * grid < ntiles) tma_issue(sm, k, &tmap, tile + k * grid, tiles_x);
+            if (tile + k * grid < ntiles) tma_issue(sm, k, p, tile + k * grid);
     unsigned phases = 0u;   // bit k: parity of the next completion of bar[k]
     for (int s = 0; tile < ntiles; tile += grid, s = s + 1 == TMA_STAGES ? 0 : s + 1) {
         const int ahead = tile + (TMA_STAGES - 1) * grid;
@@ -146,13 +174,14 @@ __global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 4 : 3)
             // stage sa was last read before the previous iteration's closing
             // barrier; order those reads before the async write
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_issue(sm, sa, &tmap, ahead, tiles_x);
+            tma_issue(sm, sa, p, ahead);
         }
         const unsigned ph = (phases >> s) & 1u;
         const bool ok = mbar_wait(&sm.bar[s], ph, wait_limit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
-                if (err) atomicExch(err, 1);
+                for (int k = 0; k < p.n; ++k)   // the tiles this CTA leaves are lost
+                    if (p.err[k]) atomicExch(p.err[k], 1);
                 // the copies in flight: this tile's and those of the next
                 // TMA_STAGES - 1 tiles
                 for (int k = 0; k < TMA_STAGES; ++k) {
@@ -164,7 +193,12 @@ __global__ void __launch_bounds__(AB_TX * AB_TY, TMA_R == 1 ? 4 : 3)
         }
         phases ^= 1u << s;
         const TmaStage& st = sm.stage[s];
-        const int x0 = (tile % tiles_x) * AB_TX, y0 = (tile / tiles_x) * TMA_TH;
+        const int lat = tma_lattice(p, tile);
+        const Args<float>& a = p.a[lat];
+        const float* __restrict__ F = static_cast<const float*>(a.f);
+        float* __restrict__ dst = p.dst[lat];
+        const int lt = tile - p.tile_begin[lat], tiles_x = p.tiles_x[lat];
+        const int x0 = (lt % tiles_x) * AB_TX, y0 = (lt / tiles_x) * TMA_TH;
         const int x = x0 + tx;
 
         // phase 1: Phi of the tile and its halo; the tile nodes keep their

@@ -86,6 +86,11 @@ template <typename S> struct Ops {
     // Persistent grid (resident CTAs per SM x SMs) of the TMA-fed two-buffer
     // kernel on the current device; 0 for formats that do not have it.
     static int tma_grid();
+    // Whether the TMA-fed two-buffer kernel advances this lattice (FP32,
+    // periodic without a mask, G_CURRENT, descriptors present).
+    static bool tma_eligible(const State& s);
+    // Two-buffer step q of n such lattices, up to 16 per launch.
+    static cudaError_t step_ab_group(const State* const* members, int n, int q, cudaStream_t st);
 };
 
 int diag_blocks(const State& s);

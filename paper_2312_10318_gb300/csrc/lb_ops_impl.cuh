@@ -75,22 +75,94 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
         v.f = s.f2;
         v.f2 = s.f;
     }
-    const Args<C> a = make_args<C>(v);
-    const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
     if constexpr (std::is_same<S, float>::value) {
-        if (!s.general && s.tma_grid > 0 && s.kerr) {
-            const int k = v.f == s.tma_buf[0] ? 0 : 1;
-            const CUtensorMap* map = static_cast<const CUtensorMap*>(s.tma_map[k]);
-            const int ntiles = (int)g.x * ((s.ny + TMA_TH - 1) / TMA_TH);
-            const int grid = ntiles < s.tma_grid ? ntiles : s.tma_grid;
-            k_step_ab_tma<S><<<grid, AB_TX * AB_TY, TMA_SMEM_BYTES, st>>>(
-                *map, a, static_cast<S*>(v.f2), (int)g.x, ntiles, s.kerr, s.wait_limit);
-            return cudaGetLastError();
+        if (tma_eligible(s)) {
+            const State* one = &s;
+            return step_ab_group(&one, 1, q, st);
         }
     }
+    const Args<C> a = make_args<C>(v);
+    const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
     if (s.general) k_step_ab<S, true><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     else k_step_ab<S, false><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     return cudaGetLastError();
+}
+
+// Dynamic shared memory and carveout of a TMA kernel; occ becomes the smaller
+// of its value and the kernel's resident CTAs per SM.
+template <typename K>
+static cudaError_t tma_setup(K kernel, int& occ) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM_BYTES);
+    // all of the unified L1/shared array as shared memory, so that the resident
+    // CTAs the occupancy query counts are the ones that run (the grid is
+    // persistent: one missing CTA per SM is a second wave)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    int o = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, AB_TX * AB_TY, TMA_SMEM_BYTES);
+    if (e == cudaSuccess) occ = occ == 0 || o < occ ? o : occ;
+    return e;
+}
+
+template <typename S>
+bool Ops<S>::tma_eligible(const State& s) {
+    return std::is_same<S, float>::value && !s.general && s.g_mode == G_CURRENT && s.tma_grid > 0 &&
+           s.kerr != nullptr;
+}
+
+// Member k of a TMA launch: lattice s at step q of a sequence (the buffers
+// alternate with q, as in step_ab); returns its tile count.
+template <int MAXL>
+static int tma_member(TmaGroup<MAXL>& g, int k, const State& s, int q) {
+    State v = s;
+    if (q & 1) {
+        v.f = s.f2;
+        v.f2 = s.f;
+    }
+    const int buf = v.f == s.tma_buf[0] ? 0 : 1;
+    g.map[k] = *static_cast<const CUtensorMap*>(s.tma_map[buf]);
+    g.a[k] = make_args<float>(v);
+    g.dst[k] = static_cast<float*>(v.f2);
+    g.err[k] = s.kerr;
+    g.tiles_x[k] = (s.nx + AB_TX - 1) / AB_TX;
+    return g.tiles_x[k] * ((s.ny + TMA_TH - 1) / TMA_TH);
+}
+
+template <int MAXL>
+static cudaError_t launch_tma(const State* const* m, int n, int q, cudaStream_t st) {
+    TmaGroup<MAXL> g;
+    g.n = n;
+    g.tile_begin[0] = 0;
+    int grid = 0;
+    long long wait = 0;
+    for (int k = 0; k < n; ++k) {
+        g.tile_begin[k + 1] = g.tile_begin[k] + tma_member(g, k, *m[k], q);
+        grid = k == 0 || m[k]->tma_grid < grid ? m[k]->tma_grid : grid;
+        wait = k == 0 || m[k]->wait_limit < wait ? m[k]->wait_limit : wait;
+    }
+    const int ntiles = g.tile_begin[n];
+    if (ntiles == 0) return cudaSuccess;
+    k_step_ab_tma<MAXL><<<ntiles < grid ? ntiles : grid, AB_TX * AB_TY, TMA_SMEM_BYTES, st>>>(g, ntiles, wait);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Ops<S>::step_ab_group(const State* const* members, int n, int q, cudaStream_t st) {
+    if constexpr (std::is_same<S, float>::value) {
+        for (int k = 0; k < n; ++k)
+            if (!tma_eligible(*members[k])) return cudaErrorInvalidValue;
+        if (n == 1) return launch_tma<1>(members, 1, q, st);
+        for (int k0 = 0; k0 < n; k0 += TMA_GROUP_MAX) {
+            const int c = n - k0 < TMA_GROUP_MAX ? n - k0 : TMA_GROUP_MAX;
+            const cudaError_t e = launch_tma<TMA_GROUP_MAX>(members + k0, c, q, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    } else {
+        (void)members; (void)n; (void)q; (void)st;
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename S>
@@ -99,15 +171,8 @@ int Ops<S>::tma_grid() {
         int dev = 0, sms = 0, occ = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaFuncSetAttribute(k_step_ab_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TMA_SMEM_BYTES) != cudaSuccess ||
-            // all of the unified L1/shared array as shared memory, so that the
-            // resident CTAs the occupancy query counts are the ones that run
-            // (the grid is persistent: one missing CTA per SM is a second wave)
-            cudaFuncSetAttribute(k_step_ab_tma<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_ab_tma<S>, AB_TX * AB_TY,
-                                                          TMA_SMEM_BYTES) != cudaSuccess)
+            tma_setup(k_step_ab_tma<1>, occ) != cudaSuccess ||
+            tma_setup(k_step_ab_tma<TMA_GROUP_MAX>, occ) != cudaSuccess)
             return 0;
         return occ * sms;
     } else {

@@ -75,7 +75,43 @@ def test_current_phi_in_batches(gpu_lib):
         batch.step(n)
     torch.cuda.synchronize()
     for a, b in pairs:
-        assert np.array_equal(a.get_f(), b.get_f())
+        fa, fb = a.get_f(), b.get_f()
+        if a.storage == "f32":
+            # the batch advances FP32 periodic lattices with the grouped TMA
+            # kernel, a separate instantiation of the single one: the compiler
+            # may contract its expressions into FMAs differently
+            assert np.abs(fa - fb).max() <= 8 * np.finfo(np.float32).eps * np.abs(fa).max()
+        else:
+            assert np.array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("shapes", [[(96, 64), (40, 33), (1, 7), (130, 9)], [(24, 16)] * 17])
+def test_tma_lattices_grouped_in_one_launch(gpu_lib, shapes):
+    """FP32 periodic current-Phi lattices of a batch share TMA launches (up to 16
+    per launch: the second case takes two); each ends where it ends alone, to
+    FP32 contraction differences, and its mass agrees to rounding."""
+    import torch
+    from paper_2312_10318_gb300.lattice import Batch
+    stream = torch.cuda.Stream()
+    pairs = []
+    for k, (nx, ny) in enumerate(shapes):
+        r = np.random.default_rng(k)
+        pr = W.Problem("r", nx, ny, 0.5 + r.uniform(0.05, 1.0), 0.5 + r.uniform(0.05, 1.5),
+                       np.zeros((ny, nx)), np.zeros((ny, nx)), g=(1e-5 * k, -2e-5))
+        f0 = W.random_populations(nx, ny, seed=100 + k, amp=0.2)
+        a = gpu_lattice(pr, "f32", "current", stream=stream).set_f(f0)
+        b = gpu_lattice(pr, "f32", "current", stream=stream).set_f(f0)
+        pairs.append((a, b))
+    batch = Batch(stream).set([b for _, b in pairs])
+    for n in (1, 6, 3):
+        for a, _ in pairs:
+            a.step(n)
+        batch.step(n)
+    torch.cuda.synchronize()
+    for a, b in pairs:
+        fa, fb = a.get_f(), b.get_f()
+        assert np.abs(fa - fb).max() <= 8 * np.finfo(np.float32).eps * np.abs(fa).max()
+        assert b.diagnostics()["mass"] == pytest.approx(a.diagnostics()["mass"], rel=1e-6)
 
 
 def test_lag_of_phi_is_a_higher_order_effect(gpu_lib):
