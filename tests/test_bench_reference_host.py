@@ -61,3 +61,23 @@ def test_cpu_baseline_reports_all_cores_and_one_core():
     assert O.num_threads() == before
     assert cb["kind"] == "oracle" and cb["cores"] == before and cb["value"] > 0
     assert cb["one_core"]["value"] > 0 and cb["cpu_model"]
+
+
+def test_grouped_current_phi_launch_count():
+    """A batch of FP32 periodic current-Phi lattices (at most 16) is one
+    TMA-fed launch per step; other formats, masks, open edges or single mode
+    keep one launch per lattice (the roofline divides by the launches)."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2312_10318_gb300 import workloads as W
+    probs = [W.double_shear_layer(64, re=1e4) for _ in range(3)]
+    a = argparse.Namespace(mode="batch", g_mode="current")
+    assert bench.tma_grouped(a, "f32", probs)
+    assert "all lattices in one launch" in bench.kernel_label(a, False, True)
+    assert not bench.tma_grouped(a, "f16", probs)
+    assert not bench.tma_grouped(argparse.Namespace(mode="single", g_mode="current"), "f32", probs)
+    assert not bench.tma_grouped(argparse.Namespace(mode="batch", g_mode="lagged"), "f32", probs)
+    assert not bench.tma_grouped(a, "f32", probs * 6)          # 18 lattices: two launches
+    ch = W.poiseuille(16, tau_s=0.8, magic=0.25)
+    assert not bench.tma_grouped(a, "f32", [ch])                # walls in y
