@@ -1,7 +1,9 @@
-"""Host-side serving logic (no GPU): the seeded stream and memory accounting."""
+"""Host-side serving logic (no GPU): the seeded stream, memory accounting and the
+precision guard's prediction."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2312_10318_gb300 import serve as S
 
@@ -48,3 +50,29 @@ def test_spec_matches_problem_parameters():
             assert math.isclose(pr.tau_s2, sp.tau_s2, rel_tol=1e-15)
             assert np.allclose(pr.g, sp.g, rtol=1e-15, atol=0)
             assert pr.mask is None
+
+
+def test_guard_prediction_is_the_linear_fit_of_two_probe_points():
+    """The guard's end-of-run prediction: with an error that grows as e0 + r t
+    it is e0 + r * steps exactly; an error that shrinks is not extrapolated
+    downwards (the growth rate is clamped at zero)."""
+
+    class Fake:
+        def __init__(self, err):
+            self.t, self.err = 0, err
+
+        def step(self, n):
+            self.t += n
+
+        def moments(self):
+            u = np.full((3, 5), self.err(self.t) * 0.04)
+            return None, u, np.zeros((3, 5))
+
+    zero = Fake(lambda t: 0.0)
+    req = S.Request(0, "taylor_green", 64, 100.0, 1000, "f32")
+    g = S.PrecisionGuard()
+    e_end, pred = g._predict(req, Fake(lambda t: 1e-6 + 2e-8 * t), zero, 0.04, 16)
+    assert e_end == pytest.approx(1e-6 + 16 * 2e-8, rel=1e-12)
+    assert pred == pytest.approx(1e-6 + 1000 * 2e-8, rel=1e-12)
+    e_end, pred = g._predict(req, Fake(lambda t: 1e-5 / (1 + t)), Fake(lambda t: 0.0), 0.04, 16)
+    assert pred == pytest.approx(e_end, rel=1e-12) and e_end == pytest.approx(1e-5 / 17, rel=1e-12)
