@@ -81,3 +81,13 @@ def test_grouped_current_phi_launch_count():
     assert not bench.tma_grouped(a, "f32", probs * 6)          # 18 lattices: two launches
     ch = W.poiseuille(16, tau_s=0.8, magic=0.25)
     assert not bench.tma_grouped(a, "f32", [ch])                # walls in y
+
+
+def test_reference_arm_follows_the_g_mode():
+    """With --g-mode current the oracle runs its current-level Phi and the line
+    names that mode in its workload."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+                        "--g-mode", "current"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.strip().startswith("{")][0])
+    assert d["config"]["workload"].endswith("G current") and d["value"] > 0
