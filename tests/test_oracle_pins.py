@@ -5,8 +5,11 @@ oracle itself: lattice isotropy and Hermite orthogonality, the equilibrium and
 source-term moment identities the paper derives (sumfeq, sumGi), conservation
 by the collision, exact special cases (tau = 1, uniform states), symmetry of
 the lattice, the Poiseuille closed form of Sec. II D (eq_a3 with the slip of
-eq_a28), Couette flow, the Taylor-Green decay of Sec. III B, and the force
-balance of a steady channel.  Everything here runs on the CPU.
+eq_a28), Couette flow, the Taylor-Green decay of Sec. III B, the force
+balance of a steady channel, the lattice-level d_gamma Phi of eq_Gi (closed-form
+central differences of rho u^3 recovered from one step, both time levels, next
+to walls), and the Galilean invariance of longitudinal-wave damping that G_i
+restores.  Everything here runs on the CPU.
 """
 import itertools
 import math
@@ -524,3 +527,223 @@ def test_taylor_green_decay_rate():
 def test_l2_norm_definition():
     """eq_n1 on a hand example: sqrt(((1-1)^2 + (2-4)^2) / (1 + 16))."""
     assert O.l2(np.array([1.0, 2.0]), np.array([1.0, 4.0])) == pytest.approx(math.sqrt(4 / 17), abs=1e-16)
+
+
+# ------------------------------------- d_gamma Phi_abg in G_i (eq_Gi, reading R1)
+#
+# A state set to its own equilibrium (no force) has no non-equilibrium part, so
+# one step of eq2 gives f* = f^eq + G_i: the lattice-level assembly of
+# d_gamma Phi (which neighbours, which sign, the factor 1/2, the time level,
+# the value beyond walls) is then visible in the post-collision moments, and
+# sumGi fixes them: sum H_ab (f* - f^eq) = -(1 - 1/(2 tau1)) d_gamma Phi_abg.
+# f* is recovered from the state after the step by undoing streaming alone
+# (eq2 left-hand side with the half-way bounce-back of eq_a20), an index shift.
+
+def _unstream(f_new, periodic, mask=None, wall_u=(0.0, 0.0), wall_rho=1.0):
+    """f*_i(x) of every node from the state after one step: f_i(x + e_i, t+1)
+    where x + e_i streams, else the bounced f_ibar(x, t+1) (plus the moving-wall
+    term 2 w_i rho_w e_i.u_w / c_s^2 at an inlet node)."""
+    e, w, cs2 = O.lattice()
+    _, ny, nx = f_new.shape
+    opp = [int(np.flatnonzero((e == -e[i]).all(axis=1))[0]) for i in range(9)]
+    out = np.zeros_like(f_new)
+    for y in range(ny):
+        for x in range(nx):
+            for i in range(9):
+                xt, yt = x + e[i, 0], y + e[i, 1]
+                inside = True
+                if not 0 <= xt < nx:
+                    inside = periodic[0]
+                    xt %= nx
+                if not 0 <= yt < ny:
+                    inside = inside and periodic[1]
+                    yt %= ny
+                c = FLUID_ if not inside else (O.FLUID if mask is None else mask[yt, xt])
+                if inside and c == O.FLUID:
+                    out[i, y, x] = f_new[i, yt, xt]
+                elif c == O.INLET:
+                    eu = e[i, 0] * wall_u[0] + e[i, 1] * wall_u[1]
+                    out[i, y, x] = f_new[opp[i], y, x] + 2.0 * w[i] * wall_rho * eu / cs2
+                else:
+                    out[i, y, x] = f_new[opp[i], y, x]
+    return out
+
+
+FLUID_ = -1   # marker: the link leaves through a non-periodic edge (a stationary wall)
+
+
+def _post_collision_moments(dfs):
+    """Moments of f* - f^eq: order 0, 1, the three H_ab and the two surviving
+    third-order components (xxy, xyy), each [ny, nx]."""
+    e, _, cs2 = O.lattice()
+    ex, ey = e[:, 0].astype(float), e[:, 1].astype(float)
+    m = lambda h: np.einsum("i,iyx->yx", h, dfs)
+    return {"0": m(np.ones(9)), "x": m(ex), "y": m(ey), "xx": m(ex * ex - cs2),
+            "yy": m(ey * ey - cs2), "xy": m(ex * ey), "xxy": m((ex * ex - cs2) * ey),
+            "xyy": m((ey * ey - cs2) * ex)}
+
+
+def _phi_fields(rho, ux, uy):
+    return rho * ux ** 3, rho * uy ** 3
+
+
+@pytest.mark.parametrize("g_mode", [O.G_CURRENT, O.G_LAGGED])
+def test_compensation_gradient_of_a_wave_along_x(g_mode):
+    """u_x = U + a sin(2 pi x / N): f* - f^eq = G_i, whose H_xx moment is
+    -(1 - 1/(2 tau1)) (Phi(x+1) - Phi(x-1)) / 2 with Phi = (U + a sin(2 pi x/N))^3
+    in closed form; every other moment of G vanishes.  A flipped sign, a lost 1/2,
+    a one-sided difference or the y neighbours in place of the x ones fail."""
+    nx, ny, U, a, tau1 = 16, 3, 0.2, 0.05, 0.8
+    x = np.arange(nx)
+    ux = np.tile(U + a * np.sin(2 * np.pi * x / nx), (ny, 1))
+    L = _lat(nx, ny, tau1, 1.3, g_mode=g_mode).init(ux, np.zeros((ny, nx)))
+    feq = L.f.copy()
+    L.step(1)
+    m = _post_collision_moments(_unstream(L.f, (True, True)) - feq)
+    phi = lambda xx: (U + a * np.sin(2 * np.pi * xx / nx)) ** 3
+    want = -(1 - 1 / (2 * tau1)) * 0.5 * (phi(x + 1) - phi(x - 1))
+    assert np.abs(want).max() > 5e-4
+    assert np.abs(m["xx"] - want[None, :]).max() < 1e-15
+    for k in ("0", "x", "y", "yy", "xy", "xxy", "xyy"):
+        assert np.abs(m[k]).max() < 1e-15, k
+
+
+@pytest.mark.parametrize("g_mode", [O.G_CURRENT, O.G_LAGGED])
+def test_compensation_gradient_of_a_wave_along_y(g_mode):
+    """u_y = V + a sin(2 pi y / N) under a uniform u_x = W: the H_yy moment of
+    f* - f^eq is -(1 - 1/(2 tau1)) d_y Phi_yyy by the central difference, and
+    H_xx gets nothing (Phi_xxx = W^3 is uniform)."""
+    nx, ny, V, W_, a, tau1 = 4, 20, -0.15, 0.07, 0.04, 0.65
+    y = np.arange(ny)
+    uy = np.tile((V + a * np.sin(2 * np.pi * y / ny))[:, None], (1, nx))
+    L = _lat(nx, ny, tau1, 2.0, g_mode=g_mode).init(np.full((ny, nx), W_), uy)
+    feq = L.f.copy()
+    L.step(1)
+    m = _post_collision_moments(_unstream(L.f, (True, True)) - feq)
+    phi = lambda yy: (V + a * np.sin(2 * np.pi * yy / ny)) ** 3
+    want = -(1 - 1 / (2 * tau1)) * 0.5 * (phi(y + 1) - phi(y - 1))
+    assert np.abs(want).max() > 1e-4
+    assert np.abs(m["yy"] - want[:, None]).max() < 1e-15
+    for k in ("0", "x", "y", "xx", "xy", "xxy", "xyy"):
+        assert np.abs(m[k]).max() < 1e-15, k
+
+
+def test_compensation_gradient_two_dimensional_field():
+    """A non-square periodic lattice with rho, u_x and u_y all varying in x and y:
+    both components of d_gamma Phi_abg at once, each from its own axis."""
+    nx, ny, tau1 = 12, 10, 0.9
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    field = lambda X, Y: (1.0 + 0.03 * np.cos(kx * X + 2 * ky * Y),
+                          0.1 + 0.05 * np.sin(kx * X) * np.cos(ky * Y),
+                          -0.08 + 0.06 * np.cos(2 * kx * X) * np.sin(ky * Y))
+    rho, ux, uy = field(X, Y)
+    L = _lat(nx, ny, tau1, 0.7, g_mode=O.G_CURRENT).init(ux, uy, rho)
+    feq = L.f.copy()
+    L.step(1)
+    m = _post_collision_moments(_unstream(L.f, (True, True)) - feq)
+    phx = lambda X, Y: _phi_fields(*field(X, Y))[0]
+    phy = lambda X, Y: _phi_fields(*field(X, Y))[1]
+    kf = 1 - 1 / (2 * tau1)
+    assert np.abs(m["xx"] + kf * 0.5 * (phx(X + 1, Y) - phx(X - 1, Y))).max() < 1e-15
+    assert np.abs(m["yy"] + kf * 0.5 * (phy(X, Y + 1) - phy(X, Y - 1))).max() < 1e-15
+    assert np.abs(m["xy"]).max() < 1e-15
+
+
+def test_lagged_compensation_uses_the_previous_level():
+    """LAGGED takes Phi of the previous step (reading R1).  A state at its own
+    equilibrium (fields B) handed a different previous Phi (of fields A) gives
+    H_aa moments from the central differences of Phi_A; CURRENT on the same input
+    uses Phi_B."""
+    nx, ny, tau1 = 14, 9, 0.75
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    fa = lambda X, Y: (1.0 + 0.0 * X, 0.12 * np.cos(kx * X), 0.09 * np.sin(ky * Y))
+    fb = lambda X, Y: (1.0 + 0.0 * X, -0.05 + 0.02 * np.sin(kx * X), 0.03 * np.cos(2 * ky * Y))
+    rho_b, ux_b, uy_b = fb(X, Y)
+    feq = _lat(nx, ny, tau1, 1.0).init(ux_b, uy_b, rho_b).f.copy()
+    phi_a = np.stack(_phi_fields(*fa(X, Y)))
+    kf = 1 - 1 / (2 * tau1)
+    for g_mode, src in ((O.G_LAGGED, fa), (O.G_CURRENT, fb)):
+        L = _lat(nx, ny, tau1, 1.0, g_mode=g_mode).set_f(feq, phi_a)
+        L.step(1)
+        m = _post_collision_moments(_unstream(L.f, (True, True)) - feq)
+        phx = lambda X, Y: _phi_fields(*src(X, Y))[0]
+        phy = lambda X, Y: _phi_fields(*src(X, Y))[1]
+        assert np.abs(m["xx"] + kf * 0.5 * (phx(X + 1, Y) - phx(X - 1, Y))).max() < 1e-15
+        assert np.abs(m["yy"] + kf * 0.5 * (phy(X, Y + 1) - phy(X, Y - 1))).max() < 1e-15
+    # and the lagged step stored Phi of its own level for the next one
+    L = _lat(nx, ny, tau1, 1.0, g_mode=O.G_LAGGED).set_f(feq, phi_a).step(1)
+    assert np.abs(L.phi - np.stack(_phi_fields(rho_b, ux_b, uy_b))).max() < 1e-16
+
+
+def test_compensation_gradient_next_to_walls_and_inlets():
+    """Reading R2: Phi is 0 beyond a stationary wall (a solid node or a
+    non-periodic edge) and rho_w u_w^3 at a moving-wall (inlet) node, so the
+    central difference next to them uses those values."""
+    nx, ny, tau1, uw = 9, 8, 0.85, (0.04, 0.03)
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[3, 4] = O.SOLID
+    mask[5, 2] = O.INLET
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    rho = 1.0 + 0.01 * np.cos(2 * np.pi * X / nx)
+    ux = 0.1 + 0.04 * np.sin(2 * np.pi * X / nx) * np.cos(np.pi * Y / ny)
+    uy = 0.05 * np.cos(2 * np.pi * X / nx) + 0.02 * Y / ny
+    L = _lat(nx, ny, tau1, 1.2, periodic_x=True, periodic_y=False, wall_ux=uw[0], wall_uy=uw[1],
+             mask=mask, g_mode=O.G_CURRENT).init(ux, uy, rho)
+    feq = L.f.copy()
+    L.step(1)
+    dfs = _unstream(L.f, (True, False), mask, uw) - feq
+    m = _post_collision_moments(dfs)
+    px, py = _phi_fields(rho, ux, uy)
+    for ph in (px, py):
+        ph[mask == O.SOLID] = 0.0
+    px[mask == O.INLET] = uw[0] ** 3
+    py[mask == O.INLET] = uw[1] ** 3
+    pyp = np.vstack([py[1:], np.zeros((1, nx))])      # beyond the edge: 0
+    pym = np.vstack([np.zeros((1, nx)), py[:-1]])
+    kf = 1 - 1 / (2 * tau1)
+    fluid = mask == O.FLUID
+    want_xx = -kf * 0.5 * (np.roll(px, -1, axis=1) - np.roll(px, 1, axis=1))
+    want_yy = -kf * 0.5 * (pyp - pym)
+    assert np.abs((m["xx"] - want_xx)[fluid]).max() < 1e-15
+    assert np.abs((m["yy"] - want_yy)[fluid]).max() < 1e-15
+    # a node next to the edge and one beside the solid really see the substitutes
+    assert abs(want_yy[0, 0]) > 1e-6 and abs(want_xx[3, 3]) > 1e-5
+
+
+def _wave_decay_rate(U, g_mode, n=64, amp=1e-3, tau=1.0, steps=600):
+    """Decay rate of the energy of a longitudinal velocity wave u_x = U + amp
+    sin(k x) on a periodic 1-D lattice, over 2 nu k^2 (nu = (tau - 1/2)/3)."""
+    k = 2 * np.pi / n
+    L = _lat(n, 1, tau, tau, g_mode=g_mode)
+    L.init((U + amp * np.sin(k * np.arange(n)))[None, :], np.zeros((1, n)))
+    ts, es = [], []
+    for s in range(0, steps + 1, 50):
+        if s:
+            L.step(50)
+        rho, ux, _ = L.moments()
+        ts.append(s)
+        es.append((CS2 * (rho - rho.mean()) ** 2 + (ux - ux.mean()) ** 2).sum())
+    slope = np.polyfit(ts, np.log(es), 1)[0]
+    return -slope / (2 * (tau - 0.5) / 3 * k * k)
+
+
+def test_compensation_restores_galilean_invariance_of_wave_damping():
+    """Physics of eq_Gi (Sec. II B): the D2Q9 equilibrium lacks rho u_x^3 in its
+    third moment (sumfeq), so the normal viscous stress of a flow along x comes
+    out as -tau rho (2 c_s^2 - 3 u_x^2) d_x u_x and a longitudinal (sound) wave
+    riding on a mean flow U is damped less, by the factor 1 - 3 U^2 / (2 c_s^2)
+    = 1 - 4.5 U^2.  G_i removes the defect: with it the damping does not depend
+    on U and equals the rest-frame value nu k^2 in amplitude (2 nu k^2 in
+    energy, the normal stress being 2 rho nu d_x u_x); without it, it follows
+    the defect.  A sign or factor error in G doubles the defect or
+    over-corrects it."""
+    for g_mode in (O.G_CURRENT, O.G_LAGGED):
+        r0, r1, r2 = (_wave_decay_rate(U, g_mode) for U in (0.0, 0.1, 0.2))
+        assert r0 == pytest.approx(1.0, abs=0.02)
+        assert r1 / r0 == pytest.approx(1.0, abs=0.003)
+        assert r2 / r0 == pytest.approx(1.0, abs=0.003)
+    r0, r1, r2 = (_wave_decay_rate(U, O.G_OFF) for U in (0.0, 0.1, 0.2))
+    assert r1 / r0 == pytest.approx(1 - 4.5 * 0.1 ** 2, abs=0.005)
+    assert r2 / r0 == pytest.approx(1 - 4.5 * 0.2 ** 2, abs=0.005)
