@@ -9,8 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_json_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
-                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+                        "--reference-seconds", "4"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
@@ -25,7 +25,8 @@ def test_reference_arm_prints_one_json_line():
 def test_reference_arm_runs_on_rank_zero_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2",
-                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+                        "--warmup", "3", "--reference-seconds", "4"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
 
@@ -87,7 +88,8 @@ def test_reference_arm_follows_the_g_mode():
     """With --g-mode current the oracle runs its current-level Phi and the line
     names that mode in its workload."""
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
-                        "--g-mode", "current"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--g-mode", "current", "--reference-seconds", "4"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads([l for l in r.stdout.splitlines() if l.strip().startswith("{")][0])
     assert d["config"]["workload"].endswith("G current") and d["value"] > 0
