@@ -173,6 +173,36 @@ int64_t trtrlb_time(trtrlb_t h);
  * out may be host or device memory. */
 int trtrlb_diagnostics(trtrlb_t h, double* out);
 
+/* Comparison of velocity fields in FP64 on the device, for the error norms of
+ * Sec. III: the relative L2 error of eq_n1, the largest local change that the
+ * steady-state test of eq_n2 divides by the characteristic speed, and the same
+ * relative L2 error of the vorticity.  The sums run over the fluid nodes of h
+ * (and pressure outlet nodes) in a fixed order, so the same fields always give
+ * the same bits.  The vorticity omega = d_x u_y - d_y u_x is taken by central
+ * differences on the node lattice at the fluid nodes whose four axis
+ * neighbours are fluid nodes of the domain (wrapped across periodic edges).
+ * out receives TRTRLB_CMP_N doubles:
+ *   [0] sqrt(sum |u - u_ref|^2 / sum |u_ref|^2)            (eq_n1 for u)
+ *   [1] max |u - u_ref|                                      (eq_n2 numerator)
+ *   [2] sqrt(sum (omega - omega_ref)^2 / sum omega_ref^2)    (eq_n1 for omega)
+ *   [3] sqrt(sum |u - u_ref|^2 / nodes)                      (RMS difference)
+ *   [4] sum |u - u_ref|^2, [5] sum |u_ref|^2,
+ *   [6] sum (omega - omega_ref)^2, [7] sum omega_ref^2,
+ *   [8] nodes compared, [9] nodes skipped because u or u_ref is not finite.
+ * A ratio with a zero denominator is 0 when its numerator is 0, else +inf.
+ * out may be host (the call then synchronises) or device memory. */
+#define TRTRLB_CMP_N 10
+
+/* u of h's current state (eq11, as trtrlb_moments gives it) against the
+ * reference fields ux_ref, uy_ref ([ny][nx] FP64, host or device; values at
+ * non-fluid nodes are ignored). */
+int trtrlb_compare(trtrlb_t h, const double* ux_ref, const double* uy_ref, double* out);
+
+/* u of a's current state against u of b's (the reference): same nx and ny;
+ * the nodes compared are a's fluid nodes.  The work runs on a's stream after
+ * the work queued so far on b's stream, and b's later work waits for it. */
+int trtrlb_compare_lattices(trtrlb_t a, trtrlb_t b, double* out);
+
 /* The same eight diagnostics as trtrlb_diagnostics, for a state given in the
  * canonical layout, computed without allocating any memory.  The paper has no
  * counterpart; this is for callers that cannot call cudaMalloc when they need

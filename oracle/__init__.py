@@ -86,6 +86,9 @@ def lib():
         L.orc_l2.argtypes = [_D, _D, C.c_int64]
         L.orc_l2.restype = C.c_double
         L.orc_drag.argtypes = [P, vp, _D, _D]
+        L.orc_max_change.argtypes = [P, vp, _D, _D, _D, _D]
+        L.orc_max_change.restype = C.c_double
+        L.orc_vorticity.argtypes = [P, vp, _D, _D, _D, _U8]
         L.orc_zou_he.argtypes = [P, vp, _D]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
@@ -245,6 +248,22 @@ def l2(qn, qa) -> float:
     return lib().orc_l2(a, b, a.size)
 
 
+def max_change(p: Params, mask, ux, uy, rx, ry) -> float:
+    """max |u - u_ref| over colliding nodes: eq_n2 before the division by u_c."""
+    a = [np.ascontiguousarray(v, np.float64) for v in (ux, uy, rx, ry)]
+    return float(lib().orc_max_change(C.byref(p.c()), _ptr(_mask(p, mask)), *a))
+
+
+def vorticity(p: Params, mask, ux, uy):
+    """(omega, valid): central-difference vorticity (reading R18) [ny, nx] and the
+    nodes where it is defined."""
+    w = np.zeros((p.ny, p.nx))
+    valid = np.zeros((p.ny, p.nx), np.uint8)
+    lib().orc_vorticity(C.byref(p.c()), _ptr(_mask(p, mask)), np.ascontiguousarray(ux, np.float64),
+                        np.ascontiguousarray(uy, np.float64), w, valid)
+    return w, valid.astype(bool)
+
+
 def num_threads() -> int:
     """OpenMP threads of the oracle's collision loop."""
     return int(lib().orc_num_threads())
@@ -266,5 +285,5 @@ def viscosity(tau1: float) -> float:
 
 
 __all__ = ["Params", "Lattice", "lattice", "hermite", "equilibrium", "forcing", "compensation",
-           "projections", "macroscopic", "collide_node", "l2", "num_threads", "set_num_threads", "tau2_from_magic", "viscosity",
+           "projections", "macroscopic", "collide_node", "l2", "max_change", "vorticity", "num_threads", "set_num_threads", "tau2_from_magic", "viscosity",
            "zou_he", "FLUID", "SOLID", "INLET", "OUTLET", "PRESSURE", "G_LAGGED", "G_CURRENT", "G_OFF"]

@@ -50,6 +50,9 @@
  *       is applied to every state the step reads or returns.  Phi beyond the
  *       edge is the outlet node's own value (zero gradient); the links that
  *       leave across the edge are open, not walls.
+ *   R18 The vorticity compared in the error norms is omega = d_x u_y - d_y u_x
+ *       by central differences on the node lattice, at fluid nodes whose four
+ *       axis neighbours are fluid nodes of the domain.
  */
 #include <math.h>
 #include <stdint.h>
@@ -550,6 +553,46 @@ double orc_l2(const double* qn, const double* qa, int64_t n) {
         den += qa[k] * qa[k];
     }
     return sqrt(num / den);
+}
+
+/* Largest local change of eq_n2's steady-state test, before the division by
+ * the characteristic speed: max over colliding nodes of |u - u_ref|. */
+double orc_max_change(const orc_params* p, const uint8_t* mask, const double* ux, const double* uy,
+                      const double* rx, const double* ry) {
+    const size_t n = (size_t)p->nx * p->ny;
+    double m = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        if (mask && !colliding(mask[k])) continue;
+        const double dx = ux[k] - rx[k], dy = uy[k] - ry[k];
+        const double d = sqrt(dx * dx + dy * dy);
+        if (d > m) m = d;
+    }
+    return m;
+}
+
+/* Vorticity omega = d_x u_y - d_y u_x by second-order central differences on
+ * the node lattice (reading R18), at colliding nodes whose four axis
+ * neighbours are colliding nodes of the domain (wrapped across periodic
+ * edges); there valid[k] = 1, elsewhere valid[k] = 0 and w[k] = 0. */
+void orc_vorticity(const orc_params* p, const uint8_t* mask, const double* ux, const double* uy,
+                   double* w, uint8_t* valid) {
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const size_t k = node(p, x, y);
+            w[k] = 0.0;
+            valid[k] = 0;
+            if (!colliding(cls(mask, p, x, y))) continue;
+            int xp = x + 1, yp = y, xm = x - 1, ym = y, xs = x, ysp = y + 1, xs2 = x, ysm = y - 1;
+            if (!wrap(p, &xp, &yp) || !wrap(p, &xm, &ym) || !wrap(p, &xs, &ysp) || !wrap(p, &xs2, &ysm))
+                continue;
+            if (!colliding(cls(mask, p, xp, yp)) || !colliding(cls(mask, p, xm, ym)) ||
+                !colliding(cls(mask, p, xs, ysp)) || !colliding(cls(mask, p, xs2, ysm)))
+                continue;
+            const double duy_dx = 0.5 * (uy[node(p, xp, yp)] - uy[node(p, xm, ym)]);
+            const double dux_dy = 0.5 * (ux[node(p, xs, ysp)] - ux[node(p, xs2, ysm)]);
+            w[k] = duy_dx - dux_dy;
+            valid[k] = 1;
+        }
 }
 
 /* Momentum-exchange force on the walls (solid class-1 nodes and the

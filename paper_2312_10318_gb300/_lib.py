@@ -16,6 +16,7 @@ F64, F32, F16_SHIFTED, BF16_SHIFTED, F64_DW = 0, 1, 2, 3, 4
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR = 0, 1, 2
+CMP_N = 10      # outputs of trtrlb_compare / trtrlb_compare_lattices
 
 # every function the header declares, with (restype, argtypes)
 _vp, _dp, _i64 = C.c_void_p, C.c_void_p, C.c_int64
@@ -47,6 +48,8 @@ SIGNATURES = {
     "trtrlb_set_f": (C.c_int, [_vp, _dp, _dp]),
     "trtrlb_time": (C.c_int64, [_vp]),
     "trtrlb_diagnostics": (C.c_int, [_vp, _dp]),
+    "trtrlb_compare": (C.c_int, [_vp, _dp, _dp, _dp]),
+    "trtrlb_compare_lattices": (C.c_int, [_vp, _vp, _dp]),
     "trtrlb_diagnostics_noalloc": (C.c_int, [_dp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_double, C.c_double, _dp, _vp]),
     "trtrlb_device_bytes": (C.c_int64, [_vp]),

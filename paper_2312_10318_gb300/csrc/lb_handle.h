@@ -18,7 +18,7 @@ struct trtrlb_lattice {
     int* ghosts;
     double* stage;       // FP64 staging for host transfers, 11 * n
     double* part;        // diagnostics partials (scratch)
-    double* dout;        // diagnostics result, 8 doubles
+    double* dout;        // result of diagnostics (8 doubles) and comparisons (TRTRLB_CMP_N)
     int64_t bytes;
     int tile_w;          // scalar-kernel tile width in the batched path (32 .. 256 nodes)
     int variant;         // TRTRLB_KERNEL_AUTO / SCALAR / VECTOR

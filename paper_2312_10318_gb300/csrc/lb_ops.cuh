@@ -95,4 +95,14 @@ template <typename S> struct Ops {
 
 int diag_blocks(const State& s);
 
+// FP64 comparison of velocity fields (compare.cu): blocks of the first level
+// (as many as diag_blocks gives for the same node count) and the launcher.
+// ux, uy, rx, ry are dense [ny][nx] device fields; mask is a lattice's pitched
+// device mask or null; part holds compare_blocks(nx * ny) * 8 doubles; out
+// receives TRTRLB_CMP_N doubles (include/trtrlb.h).
+int compare_blocks(long long nodes);
+cudaError_t compare_fields(const double* ux, const double* uy, const double* rx, const double* ry,
+                           const uint8_t* mask, int nx, int ny, int pitch, int px, int py,
+                           double* part, double* out, cudaStream_t st);
+
 }  // namespace trt

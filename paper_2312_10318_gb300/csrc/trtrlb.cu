@@ -20,6 +20,11 @@ namespace {
 
 thread_local char g_create_err[256] = "";
 
+// Device doubles of a handle's result buffer (diagnostics: 8, comparisons:
+// TRTRLB_CMP_N).
+constexpr int kResultDoubles = 16;
+static_assert(TRTRLB_CMP_N <= kResultDoubles, "comparison results exceed the result buffer");
+
 size_t elem_size(int storage) {
     switch (storage) {
         case TRTRLB_F64: return sizeof(double);
@@ -252,7 +257,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         return e == cudaSuccess;
     };
     bool ok = alloc(&h->f, es * 9 * plane) && alloc(&h->phi, ps * 4 * plane) &&
-              alloc((void**)&h->dout, sizeof(double) * 8);
+              alloc((void**)&h->dout, sizeof(double) * kResultDoubles);
     if (ok && p.g_mode == TRTRLB_G_CURRENT) ok = alloc(&h->f2, es * 9 * plane);
     if (ok && mask) ok = alloc((void**)&h->mask, (size_t)plane);
     if (ok && !ghosts.empty()) ok = alloc((void**)&h->ghosts, sizeof(int) * ghosts.size());
@@ -537,6 +542,88 @@ int trtrlb_diagnostics(trtrlb_t h, double* out) {
     if (e != cudaSuccess) return cuda_fail(h->err, e, "diagnostics");
     return dev ? TRTRLB_OK : check_kerr(h);
 }
+
+}  // extern "C"
+
+namespace {
+
+// u of h (eq11) into ux, uy (dense FP64 device fields) on `stream`.
+cudaError_t velocity_into(trtrlb_lattice* h, double* ux, double* uy, cudaStream_t stream) {
+    return TRT_DISPATCH(h->p.storage, moments(h->s, nullptr, ux, uy, stream));
+}
+
+// Comparison of a's velocity (in a's staging buffer) with rx, ry (device), into
+// out (host or device).
+int compare_into(trtrlb_lattice* a, const double* rx, const double* ry, double* out, bool host_out) {
+    const size_t n = (size_t)a->p.nx * a->p.ny;
+    cudaError_t e = trt::compare_fields(a->stage, a->stage + n, rx, ry, a->mask, a->p.nx, a->p.ny,
+                                        a->s.pitch, a->s.px, a->s.py, a->part, host_out ? a->dout : out,
+                                        a->stream);
+    if (e == cudaSuccess && host_out) {
+        e = cudaMemcpyAsync(out, a->dout, TRTRLB_CMP_N * sizeof(double), cudaMemcpyDeviceToHost,
+                            a->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(a->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(a->err, e, "compare");
+    return host_out ? check_kerr(a) : TRTRLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int trtrlb_compare(trtrlb_t h, const double* ux_ref, const double* uy_ref, double* out) {
+    if (!h) return TRTRLB_EINVAL;
+    h->err[0] = 0;
+    if (!ux_ref || !uy_ref || !out) return fail(h->err, TRTRLB_EINVAL, "ux_ref, uy_ref and out are required");
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    cudaError_t e = ensure_stage(h);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "compare staging");
+    const double* ref[2] = {ux_ref, uy_ref};
+    const double* dev[2];
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        if (on_device(ref[q])) {
+            dev[q] = ref[q];
+        } else {
+            e = cudaMemcpyAsync(h->stage + (2 + q) * n, ref[q], n * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream);
+            dev[q] = h->stage + (2 + q) * n;
+        }
+    }
+    if (e == cudaSuccess) e = velocity_into(h, h->stage, h->stage + n, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h->err, e, "compare");
+    return compare_into(h, dev[0], dev[1], out, !on_device(out));
+}
+
+int trtrlb_compare_lattices(trtrlb_t a, trtrlb_t b, double* out) {
+    if (!a || !b) return TRTRLB_EINVAL;
+    a->err[0] = 0;
+    if (!out) return fail(a->err, TRTRLB_EINVAL, "out is required");
+    if (a->p.nx != b->p.nx || a->p.ny != b->p.ny) return fail(a->err, TRTRLB_EINVAL, "lattice sizes differ");
+    const size_t n = (size_t)a->p.nx * a->p.ny;
+    cudaError_t e = ensure_stage(a);
+    if (e != cudaSuccess) return cuda_fail(a->err, e, "compare staging");
+    // b's queued work before the read of its state on a's stream, and b's
+    // later work after it
+    cudaEvent_t ev = nullptr;
+    const bool other = a->stream != b->stream;
+    if (other) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream, ev, 0);
+    }
+    if (e == cudaSuccess) e = velocity_into(b, a->stage + 2 * n, a->stage + 3 * n, a->stream);
+    if (e == cudaSuccess) e = velocity_into(a, a->stage, a->stage + n, a->stream);
+    if (e == cudaSuccess && other) e = cudaEventRecord(ev, a->stream);
+    if (e == cudaSuccess && other) e = cudaStreamWaitEvent(b->stream, ev, 0);
+    if (ev) cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(a->err, e, "compare");
+    return compare_into(a, a->stage + 2 * n, a->stage + 3 * n, out, !on_device(out));
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int64_t trtrlb_device_bytes(trtrlb_t h) { return h ? h->bytes : -1; }
 

@@ -213,6 +213,29 @@ class Lattice:
                 "wall_force_x", "wall_force_y")
         return dict(zip(keys, out.tolist()))
 
+    COMPARE_KEYS = ("l2_u", "max_du", "l2_vorticity", "rms_du", "sum_du2", "sum_uref2", "sum_dw2",
+                    "sum_wref2", "nodes", "nonfinite")
+
+    def compare(self, ref, out=None):
+        """FP64 comparison on the device of this lattice's velocity with `ref`:
+        another Lattice of the same size, or a pair (ux_ref, uy_ref) of [ny, nx]
+        float64 arrays (host or device).  Returns a dict of the outputs of
+        trtrlb_compare (include/trtrlb.h): l2_u (eq_n1), max_du (eq_n2's
+        numerator), l2_vorticity, rms_du and the raw sums; with `out` (a CUDA
+        float64 tensor of CMP_N values) the call stays asynchronous and returns
+        out."""
+        res = np.zeros(_lib.CMP_N) if out is None else out
+        if isinstance(ref, Lattice):
+            rc = self._lib.trtrlb_compare_lattices(self._h, ref._h, _ptr(res))
+        else:
+            sh = self.shape
+            ux, uy = _as_f64(ref[0], sh), _as_f64(ref[1], sh)
+            rc = self._lib.trtrlb_compare(self._h, _ptr(ux, sh), _ptr(uy, sh), _ptr(res))
+        self._chk(rc)
+        if out is not None:
+            return out
+        return dict(zip(self.COMPARE_KEYS, res.tolist()))
+
 
 class Batch:
     """Several lattices advanced together: one kernel launch per storage format and

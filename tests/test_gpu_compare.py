@@ -1,0 +1,81 @@
+"""The FP64 device comparison of velocity fields (trtrlb_compare,
+trtrlb_compare_lattices: eq_n1, eq_n2 and the vorticity norm) against the
+oracle's definitions on the same fields."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import gpu_lattice
+from paper_2312_10318_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_norms(p, mask, ux, uy, rx, ry):
+    fluid = np.ones((p.ny, p.nx), bool) if mask is None else (mask == O.FLUID) | (mask == O.PRESSURE)
+    l2 = O.l2(np.stack([ux[fluid], uy[fluid]]), np.stack([rx[fluid], ry[fluid]]))
+    w, valid = O.vorticity(p, mask, ux, uy)
+    wr, _ = O.vorticity(p, mask, rx, ry)
+    lw = O.l2(w[valid], wr[valid])
+    rms = math.sqrt(((ux - rx)[fluid] ** 2 + (uy - ry)[fluid] ** 2).sum() / fluid.sum())
+    return l2, O.max_change(p, mask, ux, uy, rx, ry), lw, rms, int(fluid.sum())
+
+
+@pytest.mark.parametrize("case", ["periodic", "walls_and_mask"])
+def test_compare_matches_oracle_norms(gpu_lib, case):
+    import torch
+    nx, ny = 131, 67
+    mask = None
+    periodic = (True, True)
+    if case == "walls_and_mask":
+        mask = W.random_mask(nx, ny, seed=4, solid_frac=0.08)
+        periodic = (True, False)
+    pr = W.Problem("random", nx, ny, 0.8, 1.1, *W.random_fields(nx, ny, seed=3)[1:], None,
+                   periodic=periodic, mask=mask)
+    lat = gpu_lattice(pr, "f64").init(pr.ux, pr.uy).step(4)
+    _, ux, uy = lat.moments()
+    _, rx, ry = W.random_fields(nx, ny, seed=11, u_amp=0.04)
+    rx, ry = ux + rx * 0.01, uy + ry * 0.01
+    p = O.Params(nx=nx, ny=ny, tau1=0.8, tau2=1.1, periodic_x=periodic[0], periodic_y=periodic[1])
+    l2, mx, lw, rms, n = _oracle_norms(p, mask, ux, uy, rx, ry)
+    for ref in ((rx, ry), tuple(torch.from_numpy(a).cuda() for a in (rx, ry))):
+        got = lat.compare(ref)
+        assert got["l2_u"] == pytest.approx(l2, rel=1e-12)
+        assert got["max_du"] == pytest.approx(mx, rel=1e-13)
+        assert got["l2_vorticity"] == pytest.approx(lw, rel=1e-12)
+        assert got["rms_du"] == pytest.approx(rms, rel=1e-12)
+        assert got["nodes"] == n and got["nonfinite"] == 0
+    # deterministic: the same fields reduce to the same bits
+    assert lat.compare((rx, ry)) == lat.compare((rx, ry))
+
+
+def test_compare_lattices_and_device_output(gpu_lib):
+    """Two lattices of one problem in FP32 and FP64: the comparison of their
+    states equals the comparison of the first with the second's moments; with a
+    device output the call queues on the stream."""
+    import torch
+    pr = W.taylor_green(96, 0.04, 200.0)
+    a = gpu_lattice(pr, "f32").init(pr.ux, pr.uy, pr.rho).step(50)
+    b = gpu_lattice(pr, "f64").init(pr.ux, pr.uy, pr.rho).step(50)
+    _, rx, ry = b.moments()
+    via_fields = a.compare((rx, ry))
+    via_lattice = a.compare(b)
+    assert via_lattice == via_fields
+    assert 1e-9 < via_lattice["l2_u"] < 1e-4
+    out = torch.empty(10, dtype=torch.float64, device="cuda")
+    a.compare(b, out=out)
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().tolist() == [via_fields[k] for k in a.COMPARE_KEYS]
+
+
+def test_compare_counts_non_finite_nodes(gpu_lib):
+    pr = W.taylor_green(32, 0.04, 100.0)
+    lat = gpu_lattice(pr, "f64").init(pr.ux, pr.uy, pr.rho)
+    _, ux, uy = lat.moments()
+    rx = ux.copy()
+    rx[3, 4] = np.nan
+    got = lat.compare((rx, uy))
+    assert got["nonfinite"] == 1 and got["nodes"] == 32 * 32 - 1
+    assert got["l2_u"] == 0.0 and got["max_du"] == 0.0

@@ -747,3 +747,51 @@ def test_compensation_restores_galilean_invariance_of_wave_damping():
     r0, r1, r2 = (_wave_decay_rate(U, O.G_OFF) for U in (0.0, 0.1, 0.2))
     assert r1 / r0 == pytest.approx(1 - 4.5 * 0.1 ** 2, abs=0.005)
     assert r2 / r0 == pytest.approx(1 - 4.5 * 0.2 ** 2, abs=0.005)
+
+
+# --------------------------------------------- error norms of Sec. III (eq_n1, eq_n2)
+
+def test_vorticity_of_a_sinusoidal_field():
+    """Reading R18: omega = d_x u_y - d_y u_x by central differences.  For
+    u_x = A cos(a x) sin(b y), u_y = B sin(a x) cos(b y) the central differences
+    of sinusoids are exact: omega = (B sin a - A sin b) cos(a x) cos(b y).  A
+    non-square periodic lattice (a != b) catches swapped axes or signs."""
+    nx, ny, A, B = 12, 20, 0.03, -0.05
+    a, b = 2 * np.pi / nx, 2 * np.pi * 2 / ny
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ux = A * np.cos(a * X) * np.sin(b * Y)
+    uy = B * np.sin(a * X) * np.cos(b * Y)
+    w, valid = O.vorticity(O.Params(nx=nx, ny=ny, tau1=1.0, tau2=1.0), None, ux, uy)
+    assert valid.all()
+    want = (B * np.sin(a) - A * np.sin(b)) * np.cos(a * X) * np.cos(b * Y)
+    assert np.abs(w - want).max() < 1e-16
+
+
+def test_vorticity_of_rigid_rotation_with_walls():
+    """A rigid rotation u = Omega (-(y - yc), x - xc) has omega = 2 Omega; central
+    differences are exact on linear fields.  Nodes on a non-periodic edge, solid
+    nodes and nodes beside a solid have no vorticity (reading R18)."""
+    nx, ny, om = 9, 7, 0.004
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[3, 5] = O.SOLID
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ux, uy = -om * (Y - 3.3), om * (X - 4.1)
+    p = O.Params(nx=nx, ny=ny, tau1=1.0, tau2=1.0, periodic_x=False, periodic_y=False)
+    w, valid = O.vorticity(p, mask, ux, uy)
+    expect = np.zeros((ny, nx), bool)
+    expect[1:-1, 1:-1] = True
+    for yy, xx in ((3, 5), (2, 5), (4, 5), (3, 4), (3, 6)):
+        expect[yy, xx] = False
+    assert np.array_equal(valid, expect)
+    assert np.abs(w[valid] - 2 * om).max() < 1e-17
+    assert (w[~valid] == 0).all()
+
+
+def test_max_change_of_eq_n2():
+    """eq_n2's numerator: the largest |u - u_ref| over fluid nodes (a solid node's
+    larger difference is ignored); hand example."""
+    p = O.Params(nx=3, ny=1, tau1=1.0, tau2=1.0)
+    mask = np.array([[0, 0, 1]], np.uint8)
+    ux, uy = np.array([[0.1, 0.3, 9.0]]), np.array([[0.0, 0.4, 0.0]])
+    rx, ry = np.array([[0.1, 0.0, 0.0]]), np.zeros((1, 3))
+    assert O.max_change(p, mask, ux, uy, rx, ry) == pytest.approx(0.5, abs=1e-16)
