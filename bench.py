@@ -386,7 +386,9 @@ def run_serving(args) -> dict:
                       "hbm_budget_gb": args.serve_budget_gb, "tuning_s_before_stream": tune_s,
                       "fp64_requests_run_as": args.serve_fp64_as},
            "batched": S.summarize(res, srv.makespan, srv.node_updates),
-           "precision_guard": {"stated_bounds": S.STATED_BOUND, "by_storage": gsum,
+           "precision_guard": {"stated_bounds": {"rule": "min(e0 + r * steps, cap), RMS |u - u_FP64| / U",
+                                                 "e0_r": S.STATED, "cap": S.ACCURACY_CAP},
+                               "by_storage": gsum,
                                "finished_in": finished}}
     if not args.no_serve_reference:
         ref = S.run_fifo(reqs, storage="f64", realtime=True)

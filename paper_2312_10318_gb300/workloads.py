@@ -106,12 +106,17 @@ def poiseuille(ny: int, tau_s: float, magic: float, nx: int = 8, u_c: float = 0.
 
 def creeping_flow(nx: int = 4096, ny: int = 2048, side: int = 64, center_x: Optional[int] = None,
                   re: float = 1.0, incompressibility: float = 0.1, magic: float = 3.0 / 16.0,
-                  steps: int = 1000, outlet: int = OUTLET) -> Problem:
+                  steps: int = 1000, outlet: int = OUTLET, ma: Optional[float] = None) -> Problem:
     """Flow past a square cylinder (Sec. III D): moving-wall inlet column x = 0
     with u_w = (u0, 0), outlet column x = nx - 1 (zero-gradient ghosts, or the
     paper's Zou-He pressure outlet at rho = 1 with outlet=PRESSURE), y periodic,
-    a side x side solid square centred at (center_x, ny/2).  Starts from rest."""
-    ma, u0, tau_s = P.creeping_flow(re, incompressibility, side)
+    a side x side solid square centred at (center_x, ny/2).  Starts from rest.
+    Ma follows T = Ma^2 / Re = incompressibility unless given."""
+    if ma is None:
+        ma, u0, tau_s = P.creeping_flow(re, incompressibility, side)
+    else:
+        u0 = ma * P.CS
+        tau_s = P.tau_from_nu(u0 * side / re)
     cx = nx // 4 if center_x is None else center_x
     mask = np.zeros((ny, nx), np.uint8)
     x0, y0 = cx - side // 2, ny // 2 - side // 2

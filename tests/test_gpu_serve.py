@@ -124,7 +124,7 @@ def test_precision_guard_falls_back_to_fp64(gpu_lib):
     # the stated bounds: FP32 keeps its format on this problem
     default = S.PrecisionGuard(probe=16)
     res = S.Server(chunk=64, guard=default).run(reqs[1:2], realtime=False)
-    assert not res[0].fallback and default.checked[0][3] < S.STATED_BOUND["f32"]
+    assert not res[0].fallback and default.checked[0][3] < S.stated_bound("f32", 320)
     # a tolerance FP16 misses but FP32 meets: the solve finishes in FP32
     mid = S.PrecisionGuard(tol=1e-4, probe=16)
     res = S.Server(chunk=64, guard=mid).run(reqs[:1], realtime=False)

@@ -68,3 +68,21 @@ def test_workload_shapes_and_seeds():
     cf = W.creeping_flow(nx=64, ny=32, side=8, re=1.0)
     assert (cf.mask[:, 0] == W.INLET).all() and (cf.mask[:, -1] == W.OUTLET).all()
     assert (cf.mask == W.SOLID).sum() == 64
+
+
+def test_creeping_flow_c4_geometry():
+    """The full-size creeping-flow lattice: 4096 x 2048, a 64 x 64 solid square
+    at x, y in [992, 1056), moving-wall inlet column, zero-gradient outlet
+    column, periodic in y; tau_{s,1} from T = Ma^2 / Re = 0.1 (1.1e5 at
+    Re = 1e-7), or from a given Ma."""
+    pr = W.creeping_flow(4096, 2048, 64, center_x=1024, re=1e-3)
+    solid = np.argwhere(pr.mask == W.SOLID)
+    assert solid[:, 1].min() == 992 and solid[:, 1].max() == 1055
+    assert solid[:, 0].min() == 992 and solid[:, 0].max() == 1055
+    assert len(solid) == 64 * 64
+    assert (pr.mask[:, 0] == W.INLET).all() and (pr.mask[:, -1] == W.OUTLET).all()
+    assert pr.periodic == (False, True)
+    assert 1.1e5 < W.creeping_flow(4096, 2048, 64, re=1e-7).tau_s < 1.11e5
+    low = W.creeping_flow(64, 32, 8, re=1.0, ma=0.1)
+    assert low.meta["u0"] == pytest.approx(0.1 / math.sqrt(3))
+    assert low.tau_s == pytest.approx(0.5 + 3 * low.meta["u0"] * 8 / 1.0)

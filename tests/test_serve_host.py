@@ -58,21 +58,36 @@ def test_guard_prediction_is_the_linear_fit_of_two_probe_points():
     downwards (the growth rate is clamped at zero)."""
 
     class Fake:
+        """A lattice whose RMS velocity difference to a resting shadow is
+        err(t) times the speed scale."""
+
         def __init__(self, err):
             self.t, self.err = 0, err
 
         def step(self, n):
             self.t += n
 
-        def moments(self):
-            u = np.full((3, 5), self.err(self.t) * 0.04)
-            return None, u, np.zeros((3, 5))
+        def compare(self, other):
+            return {"rms_du": abs(self.err(self.t) - other.err(other.t)) * 0.04}
 
     zero = Fake(lambda t: 0.0)
-    req = S.Request(0, "taylor_green", 64, 100.0, 1000, "f32")
     g = S.PrecisionGuard()
-    e_end, pred = g._predict(req, Fake(lambda t: 1e-6 + 2e-8 * t), zero, 0.04, 16)
+    e_end, pred = g._predict(1000, Fake(lambda t: 1e-6 + 2e-8 * t), zero, 0.04, 16)
     assert e_end == pytest.approx(1e-6 + 16 * 2e-8, rel=1e-12)
     assert pred == pytest.approx(1e-6 + 1000 * 2e-8, rel=1e-12)
-    e_end, pred = g._predict(req, Fake(lambda t: 1e-5 / (1 + t)), Fake(lambda t: 0.0), 0.04, 16)
+    e_end, pred = g._predict(1000, Fake(lambda t: 1e-5 / (1 + t)), Fake(lambda t: 0.0), 0.04, 16)
     assert pred == pytest.approx(e_end, rel=1e-12) and e_end == pytest.approx(1e-5 / 17, rel=1e-12)
+
+
+def test_stated_bound_grows_with_the_step_count_up_to_the_cap():
+    """The stated end-of-run error of a reduced format is e0 + r n, capped at
+    the accuracy every served result promises; the FP64 formats state 0."""
+    for st, (e0, r) in S.STATED.items():
+        assert S.stated_bound(st, 0) == pytest.approx(min(e0, S.ACCURACY_CAP))
+        assert S.stated_bound(st, 1000) == pytest.approx(min(e0 + 1000 * r, S.ACCURACY_CAP))
+        assert S.stated_bound(st, 10 ** 9) == S.ACCURACY_CAP
+    assert S.stated_bound("f32", 20000) == pytest.approx(1e-6 + 2e-3)
+    assert S.stated_bound("f64", 20000) == 0.0 and S.stated_bound("f64dw", 5) == 0.0
+    # wider formats never state a larger error for the same run
+    for n in (10, 1000, 20000):
+        assert S.stated_bound("f32", n) <= S.stated_bound("f16", n) <= S.stated_bound("bf16", n)
