@@ -105,22 +105,33 @@ def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
 
 
 # FP64 storage runs its collision on GB300's FP64 pipe, which bounds it long
-# before HBM does: its roofline is arithmetic.  128 FP64 operations per node
-# update, counted from the collision and the central differences of the step
-# (add, multiply and divide each 1; a fused multiply-add replaces two); the
-# peak is GB300's nominal dense FP64 rate (no FP64 rate is measured on the pool).
+# before HBM does: its roofline is arithmetic, against the FP64 FMA throughput
+# measured on the same GPU in the same run (trtrlb_fp64_fma_rate).  FP64
+# operations per node update (an FMA counts two): FP64_OPS_PER_NODE, from the
+# FP64 instruction counters of the step kernel (profiles/ names the capture).
 FP64_OPS_PER_NODE = 128
 FP64_NOMINAL_TFLOPS = 1.25
 
 
-def alu_roofline(storage: str, nodes_per_launch: float, launch_s: float):
+def fp64_fma_rate(stream) -> float:
+    """Measured FP64 FMA throughput of the current GPU, TFLOP/s."""
+    import ctypes as C
+    from paper_2312_10318_gb300 import _lib
+    out = C.c_double()
+    _lib.check(_lib.load().trtrlb_fp64_fma_rate(C.c_void_p(stream.cuda_stream), 0.05, C.byref(out)))
+    return out.value
+
+
+def alu_roofline(storage: str, nodes_per_launch: float, launch_s: float, peak_tflops=None):
     """The arithmetic roofline of an FP64-storage step, or None for the formats
     whose step is bound by memory traffic."""
     if storage != "f64":
         return None
     achieved = FP64_OPS_PER_NODE * nodes_per_launch / launch_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64 (not measured)",
+    peak = peak_tflops if peak_tflops else FP64_NOMINAL_TFLOPS
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_kind": "measured FP64 FMA throughput" if peak_tflops else "nominal FP64 (not measured)",
             "traffic": None, "ops_per_node": FP64_OPS_PER_NODE}
 
 
@@ -473,7 +484,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-serve-reference", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=512,
+                    help="requests in the served stream (512: the configuration's stream)")
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="Poisson arrivals per second (0: serve-load x the measured batched capacity)")
     ap.add_argument("--serve-load", type=float, default=1.2)
@@ -598,6 +610,7 @@ def main():
     clk = clocks.stop() if clocks else None
     total_ms = max_over_ranks(local_ms, dist)
     value = whole_job_rate(nodes * args.steps, world, total_ms / 1e3) / 1e6
+    fp64_tflops = fp64_fma_rate(stream)
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
     # the two-buffer (current-Phi) kernel runs one launch per lattice in a batch
@@ -654,7 +667,7 @@ def main():
                               if working_set > 4 * L2_BYTES else
                               "inputs not much larger than L2: see roofline.flushed (L2 flushed "
                               "before every step); the value is back to back")},
-            "roofline": alu_roofline(storage, nodes / per_step_launches, launch_s) or
+            "roofline": alu_roofline(storage, nodes / per_step_launches, launch_s, fp64_tflops) or
                         {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic is None else traffic,
@@ -665,6 +678,7 @@ def main():
                     "solve": f"init from pinned host fields + {args.e2e_steps} steps + fields to host"},
             "gpu_launches": launches,
             "clocks": clk,
+            "fp64_fma_tflops": fp64_tflops,
         }
         line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0], grouped)
         line["roofline"]["launch_ms"] = launch_s * 1e3

@@ -205,10 +205,10 @@ int trtrlb_compare_lattices(trtrlb_t a, trtrlb_t b, double* out);
 
 /* The same eight diagnostics as trtrlb_diagnostics, for a state given in the
  * canonical layout, computed without allocating any memory.  The paper has no
- * counterpart; this is for callers that cannot call cudaMalloc when they need
- * the numbers: code running while a stream is captured into a CUDA graph, code
- * bound to a fixed device budget or memory pool it manages itself, and
- * latency-critical loops that must not take an allocation's implicit sync.
+ * counterpart.  It is for callers that cannot call cudaMalloc when they need
+ * the numbers: a host application that hands this library only memory carved
+ * from its own pool under a fixed device budget, or a latency-critical loop
+ * that must not take the implicit synchronisation of an allocation.
  *   f      : device, 9*nx*ny FP64 populations (layout above; e.g. what
  *            trtrlb_get_f writes), read only;
  *   mask   : device, nx*ny bytes of TRTRLB_* classes, or NULL (all fluid);
@@ -222,14 +222,26 @@ int trtrlb_compare_lattices(trtrlb_t a, trtrlb_t b, double* out);
  * loading the library holds until the process exits.  Lattices of more than
  * 16,777,216 nodes (4096^2) are rejected with TRTRLB_EINVAL, as are null or
  * host pointers.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and caches it: make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (on
- * different streams, or on several host threads) race and corrupt each
- * other's results; serialise them.  Nothing needs clearing between calls:
- * every call overwrites the partial sums it reads. */
+ * (cudaGetSymbolAddress, with that device current) and caches it for the life
+ * of the process: make that first call before any stream capture, and do not
+ * call this entry point on a device after cudaDeviceReset has been called on
+ * it (the cached address no longer names the array).  All calls share the
+ * array: calls that overlap on the GPU (on different streams, or on several
+ * host threads) race and corrupt each other's results; serialise them.
+ * Nothing needs clearing between calls: every call overwrites the partial
+ * sums it reads. */
 int trtrlb_diagnostics_noalloc(const double* f, const uint8_t* mask, int32_t nx, int32_t ny,
                                int32_t periodic_x, int32_t periodic_y, double gx, double gy,
                                double* out, void* stream);
+
+/* Measured FP64 arithmetic ceiling of the current device (the paper has no
+ * counterpart): the throughput of independent chains of double-precision
+ * fused multiply-adds (2 flops each) over about `seconds` (at least 10 ms),
+ * timed with CUDA events on `stream` (cudaStream_t, NULL = legacy), written to
+ * *tflops in TFLOP/s.  FP64-storage steps, which GB300's FP64 pipe bounds long
+ * before HBM does, are reported against it.  Synchronises the stream.
+ * EINVAL for a null output or a non-positive duration, ECUDA on a CUDA error. */
+int trtrlb_fp64_fma_rate(void* stream, double seconds, double* tflops);
 
 /* Kernel shape of a lattice's step (the autotuner's knobs; results do not
  * depend on them).  variant: TRTRLB_KERNEL_AUTO (the vector kernel where it

@@ -75,6 +75,7 @@ SIGNATURES = {
     "trtrlb_slabs_slab": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "trtrlb_slabs_last_error": (C.c_char_p, [_vp]),
+    "trtrlb_fp64_fma_rate": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_double)]),
     "trtrlb_strerror": (C.c_char_p, [C.c_int]),
     "trtrlb_last_error": (C.c_char_p, [_vp]),
 }

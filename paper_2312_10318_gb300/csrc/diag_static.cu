@@ -1,15 +1,13 @@
 // FP64 lattice diagnostics that allocate nothing.
 //
-// Some callers cannot call cudaMalloc at the moment they need diagnostics:
-// code that runs while a stream is being captured into a CUDA graph (an
-// allocation there breaks the capture), code that must not grow its device
-// footprint (a host application that hands this library memory carved from
-// its own pool under a fixed budget), or code on a latency-critical path where
-// an allocation's implicit synchronisation is not acceptable.  This entry point
-// serves them: the caller passes the populations, the optional mask and the
-// output buffer, all in device memory it already owns, and the reduction's
-// per-block partial sums go to a file-scope static device array that every GPU
-// loading the library holds until the process exits.
+// Some callers cannot call cudaMalloc at the moment they need diagnostics: a
+// host application that hands this library only memory carved from its own
+// pool under a fixed device budget, or code on a latency-critical path where
+// an allocation's implicit synchronisation is not acceptable.  This entry
+// point serves them: the caller passes the populations, the optional mask and
+// the output buffer, all in device memory it already owns, and the
+// reduction's per-block partial sums go to a file-scope static device array
+// that every GPU loading the library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>

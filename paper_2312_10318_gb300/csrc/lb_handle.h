@@ -16,7 +16,8 @@ struct trtrlb_lattice {
     void* phi;           // both Phi buffers in one allocation
     uint8_t* mask;
     int* ghosts;
-    double* stage;       // FP64 staging for host transfers, 11 * n
+    double* stage;       // FP64 staging for host transfers and comparisons
+    int stage_fields;    // its size in fields of nx * ny doubles (3, 4 or 11)
     double* part;        // diagnostics partials (scratch)
     double* dout;        // result of diagnostics (8 doubles) and comparisons (TRTRLB_CMP_N)
     int64_t bytes;

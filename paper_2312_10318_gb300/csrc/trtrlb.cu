@@ -114,13 +114,27 @@ bool auto_vector(const trtrlb_lattice* h) {
     return vector_applies(h) && st != TRTRLB_F64 && st != TRTRLB_F64_DW;
 }
 
-// Staging buffer for host transfers (11 n doubles), allocated on first use.
-cudaError_t ensure_stage(trtrlb_lattice* h) {
-    if (h->stage) return cudaSuccess;
-    const size_t bytes = sizeof(double) * 11 * (size_t)h->p.nx * h->p.ny;
+// Staging buffer for host transfers and comparisons: at least `fields` FP64
+// fields of nx * ny values, allocated on first use and grown when a call needs
+// more (3 for moments and init, 4 for comparisons, 11 for populations and
+// Phi).  Growing frees the old buffer, which waits for the work queued on it.
+cudaError_t ensure_stage(trtrlb_lattice* h, int fields) {
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    if (h->stage && h->stage_fields >= fields) return cudaSuccess;
+    if (h->stage) {
+        cudaFree(h->stage);
+        h->bytes -= (int64_t)(sizeof(double) * h->stage_fields * n);
+        h->stage = nullptr;
+        h->stage_fields = 0;
+    }
+    const size_t bytes = sizeof(double) * fields * n;
     const cudaError_t e = cudaMalloc((void**)&h->stage, bytes);
-    if (e == cudaSuccess) h->bytes += (int64_t)bytes;
-    else h->stage = nullptr;
+    if (e == cudaSuccess) {
+        h->bytes += (int64_t)bytes;
+        h->stage_fields = fields;
+    } else {
+        h->stage = nullptr;
+    }
     return e;
 }
 
@@ -369,7 +383,7 @@ int trtrlb_init(trtrlb_t h, const double* rho, const double* ux, const double* u
         if (on_device(src[q])) {
             dev[q] = src[q];
         } else {
-            e = ensure_stage(h);
+            e = ensure_stage(h, 3);
             if (e != cudaSuccess) break;
             e = cudaMemcpyAsync(h->stage + q * n, src[q], nb, cudaMemcpyHostToDevice, h->stream);
             dev[q] = h->stage + q * n;
@@ -403,7 +417,7 @@ int trtrlb_moments(trtrlb_t h, double* rho, double* ux, double* uy) {
     for (int q = 0; q < 3; ++q)
         if (dst[q] && !on_device(dst[q])) host = true;
     if (host) {
-        const cudaError_t se = ensure_stage(h);
+        const cudaError_t se = ensure_stage(h, 3);
         if (se != cudaSuccess) return cuda_fail(h->err, se, "moments staging");
     }
     for (int q = 0; q < 3; ++q) {
@@ -424,7 +438,7 @@ int trtrlb_get_f(trtrlb_t h, double* f, double* phi) {
     h->err[0] = 0;
     const size_t n = (size_t)h->p.nx * h->p.ny;
     if ((f && !on_device(f)) || (phi && !on_device(phi))) {
-        const cudaError_t se = ensure_stage(h);
+        const cudaError_t se = ensure_stage(h, 11);
         if (se != cudaSuccess) return cuda_fail(h->err, se, "get_f staging");
     }
     double* df = f && !on_device(f) ? h->stage : f;
@@ -512,7 +526,7 @@ int trtrlb_set_f(trtrlb_t h, const double* f, const double* phi) {
     const double* df = f;
     const double* dp = phi;
     cudaError_t e = cudaSuccess;
-    if (!on_device(f) || (phi && !on_device(phi))) e = ensure_stage(h);
+    if (!on_device(f) || (phi && !on_device(phi))) e = ensure_stage(h, 11);
     if (e == cudaSuccess && !on_device(f)) {
         e = cudaMemcpyAsync(h->stage, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         df = h->stage;
@@ -577,7 +591,7 @@ int trtrlb_compare(trtrlb_t h, const double* ux_ref, const double* uy_ref, doubl
     h->err[0] = 0;
     if (!ux_ref || !uy_ref || !out) return fail(h->err, TRTRLB_EINVAL, "ux_ref, uy_ref and out are required");
     const size_t n = (size_t)h->p.nx * h->p.ny;
-    cudaError_t e = ensure_stage(h);
+    cudaError_t e = ensure_stage(h, 4);
     if (e != cudaSuccess) return cuda_fail(h->err, e, "compare staging");
     const double* ref[2] = {ux_ref, uy_ref};
     const double* dev[2];
@@ -601,7 +615,7 @@ int trtrlb_compare_lattices(trtrlb_t a, trtrlb_t b, double* out) {
     if (!out) return fail(a->err, TRTRLB_EINVAL, "out is required");
     if (a->p.nx != b->p.nx || a->p.ny != b->p.ny) return fail(a->err, TRTRLB_EINVAL, "lattice sizes differ");
     const size_t n = (size_t)a->p.nx * a->p.ny;
-    cudaError_t e = ensure_stage(a);
+    cudaError_t e = ensure_stage(a, 4);
     if (e != cudaSuccess) return cuda_fail(a->err, e, "compare staging");
     // b's queued work before the read of its state on a's stream, and b's
     // later work after it

@@ -40,11 +40,13 @@ def test_stability_at_re_1e7_beats_rlb(gpu_lib):
 @pytest.mark.parametrize("re,tol", [(2.0, 0.04), (20.0, 0.02)])
 def test_square_cylinder_drag_against_sen_law(gpu_lib, re, tol):
     # Sec. III D: Ma = 0.1, D = 21, L = 50 D, Zou-He outlet; Sen's empirical
-    # law for an unbounded cylinder (this box is periodic in y, blockage 1/50)
-    r = E.creeping_flow(re, ma=0.1, storage="f64dw", max_steps=150000)
+    # law for an unbounded cylinder (this box is periodic in y, blockage 1/50).
+    # The drag is taken once settled: over the last 10000 of 300000 steps C_d
+    # changes by less than 1e-5 (the L2 change of u, eq_n1, is then ~4e-8)
+    r = E.creeping_flow(re, ma=0.1, storage="f64dw", max_steps=300000)
     assert not r["diverged"], r
     (_, c1), (_, c2) = r["cd_history"][-2:]
-    assert abs(c2 / c1 - 1.0) < 1e-3, r            # C_d settling (2e-4 per 1e4 steps)
+    assert abs(c2 / c1 - 1.0) < 1e-5, r
     assert abs(r["cd"] / E.sen_drag(re) - 1.0) < tol, r
 
 

@@ -1,12 +1,13 @@
 """The allocation-free diagnostics entry point against the handle-based one.
 
-Callers that cannot call cudaMalloc at the moment they need diagnostics (a
-stream being captured into a graph, a fixed device budget managed by the host
-application, a latency-critical loop) use trtrlb_diagnostics_noalloc: they
-pass populations, mask and output in device memory they own, and the
-reduction's scratch is a static device array inside the library.  This file is
-collected last so that a stop-at-first-failure run has already run every other
-test; it also passes on its own in a fresh process.
+Callers that cannot call cudaMalloc when they need diagnostics (a host
+application that gives this library only memory from its own pool under a
+fixed budget, a latency-critical loop that must not take an allocation's
+implicit synchronisation) use trtrlb_diagnostics_noalloc: they pass
+populations, mask and output in device memory they own, and the reduction's
+scratch is a static device array inside the library.  This file is collected
+last so that a stop-at-first-failure run has already run every other test; it
+also passes on its own in a fresh process.
 """
 import ctypes as C
 
