@@ -412,6 +412,62 @@ __host__ __device__ constexpr int step_min_blocks() {
                                                                    : 1;
 }
 
+// The step of a node of a lattice periodic in x and y, without a mask.  The
+// nine slots it reads and writes are A_k = F[k][x + e_k] on an odd level (it
+// reads f_i from A_ibar and writes f*_i to A_i) and F[k][x] on an even one
+// (reads f_i from F[i][x], writes f*_i to F[ibar][x]).  Each is the node's own
+// index plus the offset k plane + e_yk pitch + e_xk, which is the same for
+// every node, plus a wrap correction that is zero away from the lattice's
+// edges: -nx for e_xk = 1 on the last column, +nx for e_xk = -1 on the first,
+// -+ plane for e_yk = +-1 on the last and first rows.  No neighbour index is
+// formed per access.
+template <typename S, bool ODD, int GMODE>
+__device__ __forceinline__ void node_step_periodic(const Args<typename Fmt<S>::C>& a, int x, int y) {
+    using C = typename Fmt<S>::C;
+    const int own = y * a.pitch + x;
+    const int pt = a.pitch;
+    const int pl = (int)a.plane;           // a plane holds at most 2^30 nodes
+    const int cxp = x == a.nx - 1 ? -a.nx : 0, cxm = x == 0 ? a.nx : 0;
+    const int cyp = y == a.ny - 1 ? -pl : 0, cym = y == 0 ? pl : 0;
+    S* __restrict__ F = static_cast<S*>(a.f);
+    C d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int k = ODD ? opp(i) : i;
+        int idx = own;
+        if (ODD) {
+            idx += ey(k) * pt + ex(k);
+            idx += ex(k) > 0 ? cxp : (ex(k) < 0 ? cxm : 0);
+            idx += ey(k) > 0 ? cyp : (ey(k) < 0 ? cym : 0);
+        }
+        d[i] = Fmt<S>::ld(F[(long long)k * a.plane + idx]);
+    }
+    C dpx = C(0), dpy = C(0);
+    if (GMODE == G_LAGGED) {
+        const C* Px = a.phi_in + own;
+        const C* Py = a.phi_in + a.plane + own;
+        dpx = C(0.5) * (Px[1 + cxp] - Px[-1 + cxm]);
+        dpy = C(0.5) * (Py[pt + cyp] - Py[-pt + cym]);
+    }
+    C o[9], phx, phy;
+    collide<C>(d, dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
+    if (GMODE == G_LAGGED) {
+        a.phi_out[own] = phx;
+        a.phi_out[a.plane + own] = phy;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int k = ODD ? i : opp(i);
+        int idx = own;
+        if (ODD) {
+            idx += ey(k) * pt + ex(k);
+            idx += ex(k) > 0 ? cxp : (ex(k) < 0 ? cxm : 0);
+            idx += ey(k) > 0 ? cyp : (ey(k) < 0 ? cym : 0);
+        }
+        F[(long long)k * a.plane + idx] = Fmt<S>::st(o[i]);
+    }
+}
+
 // One fused AA step of one node (pull-stream, moments, regularized TRT
 // collision, G_i, F_i, push-back into the same slots, half-way bounce-back);
 // non-fluid nodes return at once.  GENERAL enables walls, masks and
@@ -419,6 +475,10 @@ __host__ __device__ constexpr int step_min_blocks() {
 template <typename S, bool ODD, bool GENERAL, int GMODE>
 __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int x, int y) {
     using C = typename Fmt<S>::C;
+    if constexpr (!GENERAL) {
+        node_step_periodic<S, ODD, GMODE>(a, x, y);
+        return;
+    }
     S* __restrict__ F = static_cast<S*>(a.f);
     const int own = y * a.pitch + x;   // in-plane offsets stay below 2^30
     const int cls = (GENERAL && a.mask) ? a.mask[own] : FLUID;

@@ -79,3 +79,38 @@ def test_compare_counts_non_finite_nodes(gpu_lib):
     got = lat.compare((rx, uy))
     assert got["nonfinite"] == 1 and got["nodes"] == 32 * 32 - 1
     assert got["l2_u"] == 0.0 and got["max_du"] == 0.0
+
+
+def test_staging_grows_with_the_call(gpu_lib):
+    """The staging buffer is sized by the call: a comparison takes 4 fields of
+    nx * ny doubles, a host export of populations and Phi 11; the results do
+    not depend on the order of the calls."""
+    pr = W.taylor_green(48, 0.04, 100.0)
+    a = gpu_lattice(pr, "f32").init(pr.ux, pr.uy, pr.rho).step(7)
+    b = gpu_lattice(pr, "f64").init(pr.ux, pr.uy, pr.rho).step(7)
+    base = a.device_bytes()
+    first = a.compare(b)
+    n = 48 * 48 * 8
+    assert a.device_bytes() == base + 4 * n
+    f, phi = a.get_f(with_phi=True)
+    assert a.device_bytes() == base + 11 * n
+    assert a.compare(b) == first
+    assert np.array_equal(a.get_f(), f)
+
+
+def test_fp64_fma_rate_is_measured(gpu_lib):
+    """The FP64 ceiling the FP64-storage roofline divides by is measured on the
+    device: positive, stable between two calls, and far below the FP32 rates
+    the reduced formats run at."""
+    import ctypes as C
+    import torch
+    out = C.c_double()
+    rates = []
+    for _ in range(2):
+        assert gpu_lib.trtrlb_fp64_fma_rate(C.c_void_p(torch.cuda.current_stream().cuda_stream), 0.05,
+                                            C.byref(out)) == 0
+        rates.append(out.value)
+    print(f"FP64 FMA throughput: {rates[0]:.3f}, {rates[1]:.3f} TFLOP/s")
+    assert 0.05 < rates[0] < 100.0
+    assert abs(rates[0] / rates[1] - 1.0) < 0.1
+    assert gpu_lib.trtrlb_fp64_fma_rate(None, 0.0, C.byref(out)) == -1
