@@ -109,7 +109,7 @@ def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
 # measured on the same GPU in the same run (trtrlb_fp64_fma_rate).  FP64
 # operations per node update (an FMA counts two): FP64_OPS_PER_NODE, from the
 # FP64 instruction counters of the step kernel (profiles/ names the capture).
-FP64_OPS_PER_NODE = 128
+FP64_OPS_PER_NODE = 135
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -171,6 +171,7 @@ def tma_grouped(args, storage: str, problems) -> bool:
     """Whether a batch step of G_CURRENT lattices is one TMA-fed launch for all
     of them (FP32, periodic, no mask, at most 16 lattices)."""
     return (args.mode == "batch" and args.g_mode == "current" and storage == "f32" and len(problems) <= 16
+            and getattr(args, "kernel", "tuned") in ("tuned", "auto")
             and all(p.mask is None and all(p.periodic) for p in problems))
 
 
@@ -179,6 +180,8 @@ def kernel_label(args, vector: bool, grouped: bool = False) -> str:
     if args.g_mode == "current":
         if grouped:
             return "trt::k_step_ab_tma (two-buffer step, Phi at the current level, all lattices in one launch)"
+        if getattr(args, "kernel", "tuned") == "column":
+            return "trt::k_step_ab_col (two-buffer step walking columns, Phi at the current level, one launch per lattice)"
         return "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)"
     if args.mode == "batch":
         return ("trt::k_step_group_vec" if vector else "trt::k_step_group") + \
@@ -476,7 +479,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", default=None, help="override the lattice size, NXxNY")
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16", "f64dw"])
-    ap.add_argument("--kernel", default="tuned", choices=["tuned", "auto", "scalar", "vector"],
+    ap.add_argument("--kernel", default="tuned", choices=["tuned", "auto", "scalar", "vector", "column"],
                     help="tuned: the autotuner picks the kernel shape per lattice (default)")
     ap.add_argument("--tile-w", type=int, default=0, help="scalar kernel tile width (with --kernel scalar)")
     ap.add_argument("--g-mode", default="lagged", choices=["lagged", "current", "off"],

@@ -88,6 +88,10 @@ extern "C" {
                            for a fluid node another sub-lattice updates; it
                            does not collide, links into it stream, and its
                            populations and Phi are written by the exchange  */
+#define TRTRLB_HALO_PRESSURE 6 /* halo node standing for a TRTRLB_PRESSURE node
+                           another sub-lattice updates: as TRTRLB_HALO, and a
+                           Phi taken from its populations (G_CURRENT) takes
+                           the Zou-He rebuild first, as the owner's does    */
 
 /* Problem statement (Sec. II B, eq2; eq_mu; eq_a2; eq_a29). */
 typedef struct {
@@ -251,11 +255,16 @@ int trtrlb_fp64_fma_rate(void* stream, double seconds, double* tflops);
  * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
  * lattice is periodic in both directions, has no mask and nx is a multiple
  * of that width).
+ * TRTRLB_KERNEL_COLUMN (G_CURRENT only: the two-buffer kernel whose warps walk
+ * down bands of 64 rows of 30 columns, keeping the Phi of the rows above and
+ * below in registers; ENOTSUP unless the lattice is periodic in both
+ * directions, has no mask and stores FP64, FP32, FP16 or BF16).
  * tile_w: width in nodes of the scalar kernel's 256-thread tile (32, 64, 128
  * or 256; 0 keeps the current one). */
 #define TRTRLB_KERNEL_AUTO 0
 #define TRTRLB_KERNEL_SCALAR 1
 #define TRTRLB_KERNEL_VECTOR 2
+#define TRTRLB_KERNEL_COLUMN 3
 int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w);
 
 /* Checkpoint and resume (the paper has none): the raw device state -- the
@@ -295,8 +304,12 @@ int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w);
  * device copies on the slabs' stream: before it, the previous level's
  * Phi_yyy of the boundary rows (LAGGED); around a step from an odd level of
  * the in-place pattern, the y-moving populations of the boundary rows (in
- * before, out after).  Results equal the undivided lattice's bit for bit.
- * G_CURRENT and masks with outlet ghosts (or halo nodes) give ENOTSUP; host or
+ * before, out after); around a two-buffer step (G_CURRENT), all nine
+ * populations of the boundary rows before it (the halo's Phi is then taken at
+ * the current level from them) and the populations pushed into the halo rows
+ * after it.  Results equal the undivided lattice's bit for bit (G_CURRENT in
+ * FP32 against its plain two-buffer kernel: the TMA-fed one contracts into FMAs
+ * differently).  Masks with outlet ghosts (or halo nodes) give ENOTSUP; host or
  * device pointers are accepted where fields are passed (global [ny][nx] /
  * [9][ny][nx] layouts); calls synchronise except step. */
 typedef struct trtrlb_slabs* trtrlb_slabs_t;

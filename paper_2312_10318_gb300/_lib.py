@@ -15,7 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5,
 F64, F32, F16_SHIFTED, BF16_SHIFTED, F64_DW = 0, 1, 2, 3, 4
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR = 0, 1, 2
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_COLUMN = 0, 1, 2, 3
 CMP_N = 10      # outputs of trtrlb_compare / trtrlb_compare_lattices
 
 # every function the header declares, with (restype, argtypes)

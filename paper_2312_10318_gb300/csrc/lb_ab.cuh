@@ -64,7 +64,7 @@ __device__ __forceinline__ void ab_phi(const Args<typename Fmt<S>::C>& a, const 
     C d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = Fmt<S>::ld(F[(long long)i * a.plane + k]);
-    if (c == PRESSURE) zh_fill<C>(d, a.zh_dr);
+    if (c == PRESSURE || c == HALO_PRESSURE) zh_fill<C>(d, a.zh_dr);
     C rho, ux, uy;
     moments_of<C>(d, a.gx, a.gy, a.rho0, rho, ux, uy);
     px = rho * ux * ux * ux;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(AB_TX * AB_TY, 4) k_step_ab(Args<typename Fmt<
     for (int i = 0; i < 9; ++i) {
         int txn = x + ex(i), tyn = y + ey(i);
         const int c = i == 0 ? FLUID : ab_class(a, txn, tyn);
-        if (collides(c) || c == HALO) {
+        if (collides(c) || c == HALO || c == HALO_PRESSURE) {
             dst[(long long)i * a.plane + (long long)tyn * a.pitch + txn] = Fmt<S>::st(o[i]);
         } else if (c == SOLID || c == AB_OUT) {
             // (across the edge of a pressure outlet this fills a population

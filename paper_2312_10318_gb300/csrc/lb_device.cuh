@@ -35,7 +35,7 @@ __host__ __device__ constexpr double wgt(int i) {
     return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-enum : uint8_t { FLUID = 0, SOLID = 1, INLET = 2, OUTLET = 3, PRESSURE = 4, HALO = 5 };
+enum : uint8_t { FLUID = 0, SOLID = 1, INLET = 2, OUTLET = 3, PRESSURE = 4, HALO = 5, HALO_PRESSURE = 6 };
 
 // Classes whose nodes collide: fluid nodes and Zou-He pressure outlet nodes.
 __host__ __device__ constexpr bool collides(int c) { return c == FLUID || c == PRESSURE; }

@@ -44,6 +44,7 @@ struct State {
     int px, py;
     bool general;         // walls, mask or non-periodic edges present
     bool vec;             // the vectorised kernel runs this lattice
+    bool col;             // G_CURRENT: the column-walking two-buffer kernel runs it
     int tile_w;           // scalar kernels: block of tile_w x (256 / tile_w) nodes
     int g_mode;
     double tau1, tau2, gx, gy, rho0;

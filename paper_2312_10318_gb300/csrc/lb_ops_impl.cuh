@@ -3,6 +3,7 @@
 #include <type_traits>
 
 #include "lb_ab.cuh"
+#include "lb_ab_col.cuh"
 #include "lb_ab_tma.cuh"
 #include "lb_aux.cuh"
 #include "lb_batch.cuh"
@@ -82,6 +83,15 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
         }
     }
     const Args<C> a = make_args<C>(v);
+    if constexpr (!std::is_same<S, f64dw>::value) {
+        if (s.col && !s.general) {
+            const int gx = (s.nx + COL_W - 1) / COL_W, bands = (s.ny + COL_H - 1) / COL_H;
+            const long long warps = (long long)gx * bands;
+            const int blocks = (int)((warps + COL_WARPS - 1) / COL_WARPS);
+            k_step_ab_col<S><<<blocks, COL_WARPS * 32, 0, st>>>(a, static_cast<S*>(v.f2), gx, bands);
+            return cudaGetLastError();
+        }
+    }
     const dim3 g((s.nx + AB_TX - 1) / AB_TX, (s.ny + AB_TY - 1) / AB_TY);
     if (s.general) k_step_ab<S, true><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);
     else k_step_ab<S, false><<<g, AB_TX * AB_TY, 0, st>>>(a, static_cast<S*>(v.f2), 0);

@@ -1,12 +1,17 @@
 // Slab decomposition: one lattice split into sub-lattices of consecutive rows,
 // each a lattice handle of its own with halo rows (class TRTRLB_HALO) facing
-// its neighbours, and a row exchange between time steps.  The exchange follows
-// the in-place AA pattern: a step from an even level touches only each node's
-// own populations, so it needs nothing from the neighbours but the previous
-// level's Phi_yyy row (for d_y Phi_yyy of G_i, eq_Gi); a step from an odd level
-// reads the populations its neighbour row left in it and pushes populations
-// into that row, so the boundary rows' y-moving slots are copied into the halo
-// rows before it and back out of them after it.
+// its neighbours, and a row exchange between time steps.  With Phi lagged (or
+// no G) the exchange follows the in-place AA pattern: a step from an even
+// level touches only each node's own populations, so it needs nothing from the
+// neighbours but the previous level's Phi_yyy row (for d_y Phi_yyy of G_i,
+// eq_Gi); a step from an odd level reads the populations its neighbour row left
+// in it and pushes populations into that row, so the boundary rows' y-moving
+// slots are copied into the halo rows before it and back out of them after it.
+// With Phi at the current level the two-buffer step computes Phi of every
+// neighbour from its populations, so all nine populations of each boundary row
+// go into the facing halo row before the step (the halo node's Phi is then the
+// one the undivided lattice computes), and what the step pushed into the halo
+// rows goes back to the rows that own it afterwards.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -58,8 +63,9 @@ int local_last(const trtrlb_slabs* s, int k) { return s->lo_halo[k] + s->rows[k]
 
 // Copies row `src_row` of planes `planes` of slab a's current populations into
 // row `dst_row` of slab b.
+template <int NP>
 cudaError_t copy_pops(trtrlb_slabs* s, trtrlb_t a, int src_row, trtrlb_t b, int dst_row,
-                      const int (&planes)[3]) {
+                      const int (&planes)[NP]) {
     const size_t es = pop_bytes(s->p.storage);
     const size_t row = (size_t)s->p.nx * es;
     for (int q : planes) {
@@ -81,6 +87,7 @@ cudaError_t copy_phi_y(trtrlb_slabs* s, trtrlb_t a, int src_row, trtrlb_t b, int
 
 constexpr int kUp[3] = {2, 5, 6};     // e_y = +1
 constexpr int kDown[3] = {4, 7, 8};   // e_y = -1
+constexpr int kAll[9] = {0, 1, 2, 3, 4, 5, 6, 7, 8};
 
 // Copies the slots (i, x) of one halo row that the step's push wrote, i in
 // {i0, i1, i2}: those whose writer, the node x - e_i of the facing boundary
@@ -133,10 +140,13 @@ cudaError_t copy_out(trtrlb_slabs* s, trtrlb_t a, int a_row, trtrlb_t b, int b_r
 //        facing halo row: an odd-level state keeps f_i(x) with e_iy = -1 of a
 //        top row in the e_y = +1 slots of the row above (and the converse), so
 //        both the next step's pull and any read of the state need them;
-//   OUT: after a step from an odd level, what the push left in each halo row
-//        (the e_y = +1 slots above a top row, e_y = -1 below a bottom row)
-//        back into the row that owns it, slot by slot where the push wrote.
-enum Part { PHI, IN, OUT };
+//   OUT: after a step from an odd level, or after a two-buffer step (Phi at
+//        the current level), what the push left in each halo row (the e_y = +1
+//        slots above a top row, e_y = -1 below a bottom row) back into the row
+//        that owns it, slot by slot where the push wrote;
+//   ROWS: before a two-buffer step, all nine populations of each boundary row
+//        into the facing halo row.
+enum Part { PHI, IN, OUT, ROWS };
 
 cudaError_t exchange(trtrlb_slabs* s, Part part) {
     const int n = (int)s->slab.size();
@@ -153,6 +163,9 @@ cudaError_t exchange(trtrlb_slabs* s, Part part) {
         } else if (part == IN) {
             e = copy_pops(s, B, b_bot, A, a_halo, kUp);
             if (e == cudaSuccess) e = copy_pops(s, A, a_top, B, b_halo, kDown);
+        } else if (part == ROWS) {
+            e = copy_pops(s, B, b_bot, A, a_halo, kAll);
+            if (e == cudaSuccess) e = copy_pops(s, A, a_top, B, b_halo, kAll);
         } else {
             e = copy_out(s, A, a_halo, B, b_bot, A, a_top, kUp);
             if (e == cudaSuccess) e = copy_out(s, B, b_halo, A, a_top, B, b_bot, kDown);
@@ -177,11 +190,11 @@ int trtrlb_slabs_create(const trtrlb_params* pp, const uint8_t* mask, int32_t ns
                         trtrlb_slabs_t* out) {
     if (!pp || !out || nslabs < 1) return TRTRLB_EINVAL;
     const trtrlb_params p = *pp;
-    if (p.g_mode == TRTRLB_G_CURRENT) return TRTRLB_ENOTSUP;
     if (p.ny < nslabs || p.nx < 1) return TRTRLB_EINVAL;
     if (mask) {
         for (long long k = 0; k < (long long)p.nx * p.ny; ++k)
-            if (mask[k] == TRTRLB_OUTLET || mask[k] == TRTRLB_HALO) return TRTRLB_ENOTSUP;
+            if (mask[k] == TRTRLB_OUTLET || mask[k] == TRTRLB_HALO || mask[k] == TRTRLB_HALO_PRESSURE)
+                return TRTRLB_ENOTSUP;
     }
     trtrlb_slabs* s = new (std::nothrow) trtrlb_slabs();
     if (!s) return TRTRLB_ENOMEM;
@@ -212,9 +225,11 @@ int trtrlb_slabs_create(const trtrlb_params* pp, const uint8_t* mask, int32_t ns
             const bool halo = (lo && r == 0) || (hi && r == q.ny - 1);
             for (int x = 0; x < p.nx; ++x) {
                 uint8_t c = global_class(gy, x);
-                // a halo node stands for a node another slab updates; walls and
+                // a halo node stands for a node another slab updates (a pressure
+                // outlet node keeps its Zou-He rebuild for Phi); walls and
                 // moving walls keep their class (they do not update anyway)
-                if (halo && (c == TRTRLB_FLUID || c == TRTRLB_PRESSURE)) c = TRTRLB_HALO;
+                if (halo && c == TRTRLB_FLUID) c = TRTRLB_HALO;
+                else if (halo && c == TRTRLB_PRESSURE) c = TRTRLB_HALO_PRESSURE;
                 m[(size_t)r * p.nx + x] = c;
             }
         }
@@ -283,6 +298,19 @@ int trtrlb_slabs_init(trtrlb_slabs_t s, const double* rho, const double* ux, con
 int trtrlb_slabs_step(trtrlb_slabs_t s, int64_t nsteps) {
     if (!s || nsteps < 0) return TRTRLB_EINVAL;
     s->err[0] = 0;
+    if (s->p.g_mode == TRTRLB_G_CURRENT) {
+        for (int64_t t = 0; t < nsteps; ++t) {
+            cudaError_t e = exchange(s, ROWS);
+            if (e != cudaSuccess) return cuda_fail(s, e, "halo exchange");
+            for (trtrlb_t h : s->slab) {
+                const int rc = trtrlb_step(h, 1);
+                if (rc != TRTRLB_OK) return lattice_fail(s, h, rc);
+            }
+            e = exchange(s, OUT);
+            if (e != cudaSuccess) return cuda_fail(s, e, "halo exchange");
+        }
+        return TRTRLB_OK;
+    }
     for (int64_t t = 0; t < nsteps; ++t) {
         const bool odd = odd_level(s);
         cudaError_t e = s->p.g_mode == TRTRLB_G_LAGGED ? exchange(s, PHI) : cudaSuccess;

@@ -233,7 +233,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         for (int y = 0; y < p.ny; ++y)
             for (int x = 0; x < p.nx; ++x) {
                 const uint8_t c = mask[(long long)y * p.nx + x];
-                if (c > TRTRLB_HALO) return fail(err, TRTRLB_EINVAL, "mask class out of range");
+                if (c > TRTRLB_HALO_PRESSURE) return fail(err, TRTRLB_EINVAL, "mask class out of range");
                 if (c == TRTRLB_PRESSURE && (p.periodic_x || x != p.nx - 1))
                     return fail(err, TRTRLB_EINVAL,
                                 "pressure outlet nodes must lie on the last column of a lattice not periodic in x");
@@ -657,12 +657,20 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
                             "the vector kernel needs a periodic lattice without mask and nx divisible by its width");
             vec = true;
             break;
+        case TRTRLB_KERNEL_COLUMN:
+            if (h->p.g_mode != TRTRLB_G_CURRENT || h->s.general || h->p.storage == TRTRLB_F64_DW)
+                return fail(h->err, TRTRLB_ENOTSUP,
+                            "the column kernel needs G_CURRENT, a periodic lattice without mask and FP64, FP32, FP16 or BF16 storage");
+            vec = false;
+            break;
         default: return fail(h->err, TRTRLB_EINVAL, "unknown kernel variant");
     }
     h->variant = variant;
     h->s.vec = vec;
-    // G_CURRENT: AUTO runs the TMA-fed kernel where it exists, SCALAR the plain one
-    h->s.tma_grid = variant == TRTRLB_KERNEL_SCALAR ? 0 : h->tma_grid;
+    h->s.col = variant == TRTRLB_KERNEL_COLUMN;
+    // G_CURRENT: AUTO runs the TMA-fed kernel where it exists, SCALAR the plain
+    // one, COLUMN the column-walking one
+    h->s.tma_grid = variant == TRTRLB_KERNEL_AUTO || variant == TRTRLB_KERNEL_VECTOR ? h->tma_grid : 0;
     if (tile_w) h->tile_w = h->s.tile_w = tile_w;
     return TRTRLB_OK;
 }

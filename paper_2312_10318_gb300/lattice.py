@@ -143,8 +143,10 @@ class Lattice:
         self._stream = s
 
     def set_kernel(self, variant="auto", tile_w=0):
-        """Kernel shape: 'auto' | 'scalar' | 'vector', scalar tile width (0 keeps it)."""
-        v = {"auto": _lib.KERNEL_AUTO, "scalar": _lib.KERNEL_SCALAR, "vector": _lib.KERNEL_VECTOR}[variant]
+        """Kernel shape: 'auto' | 'scalar' | 'vector' | 'column' (G_CURRENT), scalar
+        tile width (0 keeps it)."""
+        v = {"auto": _lib.KERNEL_AUTO, "scalar": _lib.KERNEL_SCALAR, "vector": _lib.KERNEL_VECTOR,
+             "column": _lib.KERNEL_COLUMN}[variant]
         self._chk(self._lib.trtrlb_set_kernel(self._h, v, int(tile_w)))
         return self
 
@@ -286,7 +288,7 @@ class Slabs:
     """One lattice split into `nslabs` sub-lattices of consecutive rows with a
     one-row halo exchange between steps (the single-device form of a domain
     split; results equal the undivided Lattice bit for bit).  Arguments as for
-    Lattice; G mode 'lagged' or 'off'; no outlet ghosts in the mask."""
+    Lattice, any G mode; no outlet ghosts in the mask."""
 
     def __init__(self, nx, ny, tau_s, nslabs, *, tau_s2=None, magic=None, periodic=(True, True),
                  g=(0.0, 0.0), rho0=1.0, wall_u=(0.0, 0.0), wall_rho=1.0, outlet_rho=1.0,

@@ -85,9 +85,11 @@ def test_staging_grows_with_the_call(gpu_lib):
     """The staging buffer is sized by the call: a comparison takes 4 fields of
     nx * ny doubles, a host export of populations and Phi 11; the results do
     not depend on the order of the calls."""
+    import torch
     pr = W.taylor_green(48, 0.04, 100.0)
-    a = gpu_lattice(pr, "f32").init(pr.ux, pr.uy, pr.rho).step(7)
-    b = gpu_lattice(pr, "f64").init(pr.ux, pr.uy, pr.rho).step(7)
+    dev = [torch.from_numpy(v).cuda() for v in (pr.ux, pr.uy, pr.rho)]   # no host staging
+    a = gpu_lattice(pr, "f32").init(*dev).step(7)
+    b = gpu_lattice(pr, "f64").init(*dev).step(7)
     base = a.device_bytes()
     first = a.compare(b)
     n = 48 * 48 * 8

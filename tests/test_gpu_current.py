@@ -199,3 +199,60 @@ def test_tma_wait_that_runs_out_is_reported(gpu_lib):
     R = oracle_lattice(pr, "current").init(pr.ux, pr.uy, pr.rho)
     R.step(10)
     assert max(field_errors(G, R).values()) < 1e-5
+
+
+@pytest.mark.parametrize("nx,ny", [(7, 5), (33, 17), (64, 64), (130, 9), (1, 8), (8, 1), (1, 1), (61, 131),
+                                   (30, 64), (31, 65)])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_column_kernel_matches_oracle(gpu_lib, nx, ny, storage):
+    """The column-walking two-buffer kernel (warps walking bands of 64 rows of
+    30 columns; lanes beside the group give the neighbours' Phi by shuffle, the
+    rows above and below are kept from the walk) against the oracle's CURRENT
+    mode on periodic lattices of sizes that leave partial groups and bands,
+    wrap within one group, or have one row or column: FP64 to 1e-12 per field,
+    FP32 every field within its rounding bounds."""
+    from helpers import check_rounding_bounds, shifted_max
+    r = np.random.default_rng(7 * nx + ny)
+    pr = W.Problem("r", nx, ny, 0.5 + r.uniform(0.02, 1.5), 0.5 + r.uniform(0.02, 1.5),
+                   np.zeros((ny, nx)), np.zeros((ny, nx)), g=(1e-4, -2e-5))
+    f0 = W.random_populations(nx, ny, seed=nx * 5 + ny, amp=0.3)
+    G = gpu_lattice(pr, storage, "current").set_kernel("column").set_f(f0)
+    R = oracle_lattice(pr, "current").set_f(f0)
+    d_max = shifted_max(R)
+    done = 0
+    for n in (1, 2, 5):
+        G.step(n - done)
+        R.step(n - done)
+        done = n
+        if storage == "f64":
+            errs = field_errors(G, R)
+            assert max(errs.values()) < 1e-12, (n, errs)
+        else:
+            check_rounding_bounds("f32", G, R, n, max(d_max, shifted_max(R)))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_column_kernel_taylor_green(gpu_lib, storage):
+    """The column kernel on the 64^2 Taylor-Green vortex over 1000 steps in the
+    reduced formats: every field within the rounding bounds of the format
+    against the oracle's CURRENT mode."""
+    from helpers import check_rounding_bounds, shifted_max
+    pr = W.taylor_green(64, 0.04, 100.0, magic=0.25)
+    G = gpu_lattice(pr, storage, "current").set_kernel("column").init(pr.ux, pr.uy, pr.rho)
+    R = oracle_lattice(pr, "current").init(pr.ux, pr.uy, pr.rho)
+    d_max = shifted_max(R)
+    G.step(1000)
+    R.step(1000)
+    check_rounding_bounds(storage, G, R, 1000, d_max)
+
+
+def test_column_kernel_only_where_it_applies(gpu_lib):
+    from paper_2312_10318_gb300._lib import TrtrlbError
+    pr = W.taylor_green(32, 0.04, 100.0)
+    for kw, storage in ((dict(g_mode="lagged"), "f32"), (dict(g_mode="current"), "f64dw")):
+        lat = gpu_lattice(pr, storage, **kw)
+        with pytest.raises(TrtrlbError):
+            lat.set_kernel("column")
+    ch = W.poiseuille(16, 0.8, 0.25)
+    with pytest.raises(TrtrlbError):
+        gpu_lattice(ch, "f32", "current").set_kernel("column")

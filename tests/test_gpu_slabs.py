@@ -36,6 +36,44 @@ def test_slabs_equal_the_whole_lattice(gpu_lib, storage, g_mode, periodic, nx, n
     assert b["max_u"] == a["max_u"]
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "f64dw"])
+@pytest.mark.parametrize("periodic", [(True, True), (True, False), (False, True)])
+@pytest.mark.parametrize("nx,ny,nslabs", [(37, 23, 2), (40, 23, 3), (33, 5, 5)])
+def test_slabs_with_current_phi_equal_the_whole_lattice(gpu_lib, storage, periodic, nx, ny, nslabs):
+    """Phi at the current level (the two-buffer step): the boundary rows' nine
+    populations reach the facing halo rows before each step, so every halo
+    node's Phi is the undivided lattice's; the pushes into the halo rows go back
+    after it.  The undivided lattice runs the plain two-buffer kernel (the
+    TMA-fed FP32 one contracts differently, by a few ulps)."""
+    rho, ux, uy = W.random_fields(nx, ny, seed=3 * nx + ny)
+    whole, slabs = _pair(nx, ny, nslabs, storage, "current", periodic)
+    whole.set_kernel("scalar")
+    whole.init(ux, uy, rho)
+    slabs.init(ux, uy, rho)
+    for n in (1, 1, 6, 25):
+        whole.step(n)
+        slabs.step(n)
+        assert np.array_equal(slabs.get_f(), whole.get_f()), (n, storage)
+    a, b = whole.diagnostics(), slabs.diagnostics()
+    assert b["mass"] == pytest.approx(a["mass"], rel=1e-13)
+
+
+def test_slabs_with_current_phi_walls_and_pressure_outlet(gpu_lib):
+    nx, ny = 45, 26
+    mask = W.random_mask(nx, ny, seed=7, solid_frac=0.1, inlet_outlet=True, outlet=W.PRESSURE)
+    rho, ux, uy = W.random_fields(nx, ny, seed=7)
+    whole, slabs = _pair(nx, ny, 4, "f64", "current", (False, True), mask=mask, wall_u=(0.03, 0.0))
+    whole.init(ux, uy, rho)
+    slabs.init(ux, uy, rho)
+    live = (mask == O.FLUID) | (mask == O.PRESSURE)
+    for n in (1, 3, 16):
+        whole.step(n)
+        slabs.step(n)
+        assert np.array_equal(slabs.get_f()[:, live], whole.get_f()[:, live]), n
+    a, b = whole.diagnostics(), slabs.diagnostics()
+    assert b["wall_force_x"] == pytest.approx(a["wall_force_x"], rel=1e-12, abs=1e-15)
+
+
 @pytest.mark.parametrize("outlet", [None, W.PRESSURE])
 @pytest.mark.parametrize("seed", range(2))
 def test_slabs_with_walls_inlet_and_pressure_outlet(gpu_lib, outlet, seed):
@@ -72,8 +110,6 @@ def test_one_slab_is_the_lattice(gpu_lib):
 
 def test_unsupported_slab_configurations(gpu_lib):
     from paper_2312_10318_gb300._lib import TrtrlbError
-    with pytest.raises(TrtrlbError):
-        Slabs(16, 16, 0.8, 2, tau_s2=1.0, g_mode="current")
     m = W.random_mask(16, 16, seed=0, solid_frac=0.0, inlet_outlet=True)   # outlet ghosts
     with pytest.raises(TrtrlbError):
         Slabs(16, 16, 0.8, 2, tau_s2=1.0, periodic=(False, True), mask=m)
