@@ -167,21 +167,33 @@ def kernel_source_hash(csrc: str | None = None) -> str:
     return h.hexdigest()[:16]
 
 
+# lattices below this many nodes share the TMA-fed launches of a batch (the
+# library's rule); larger ones take a launch each
+TMA_SHARE_MAX_NODES = 2048 * 2048
+
+
 def tma_grouped(args, storage: str, problems) -> bool:
     """Whether a batch step of G_CURRENT lattices is one TMA-fed launch for all
     of them (FP32, periodic, no mask, at most 16 lattices)."""
     return (args.mode == "batch" and args.g_mode == "current" and storage == "f32" and len(problems) <= 16
             and getattr(args, "kernel", "tuned") in ("tuned", "auto")
-            and all(p.mask is None and all(p.periodic) for p in problems))
+            and all(p.mask is None and all(p.periodic) and p.nodes < TMA_SHARE_MAX_NODES for p in problems))
 
 
-def kernel_label(args, vector: bool, grouped: bool = False) -> str:
-    """Name of the step kernel the timed region launches."""
+def kernel_label(args, vector: bool, grouped: bool = False, storage: str = "f32", problems=()) -> str:
+    """Name of the step kernel the timed region launches (the library's choice
+    for the lattice's format, G mode, boundaries and size, or the one forced)."""
     if args.g_mode == "current":
         if grouped:
             return "trt::k_step_ab_tma (two-buffer step, Phi at the current level, all lattices in one launch)"
-        if getattr(args, "kernel", "tuned") == "column":
+        plain_periodic = all(p.mask is None and all(p.periodic) for p in problems)
+        k = getattr(args, "kernel", "tuned")
+        auto = k in ("tuned", "auto")
+        if k == "column" or (auto and plain_periodic and storage in ("f64", "f16", "bf16")
+                             and all(p.nodes >= 512 * 512 for p in problems)):
             return "trt::k_step_ab_col (two-buffer step walking columns, Phi at the current level, one launch per lattice)"
+        if auto and plain_periodic and storage == "f32":
+            return "trt::k_step_ab_tma (two-buffer step fed by TMA, Phi at the current level, one launch per lattice)"
         return "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)"
     if args.mode == "batch":
         return ("trt::k_step_group_vec" if vector else "trt::k_step_group") + \
@@ -683,7 +695,7 @@ def main():
             "clocks": clk,
             "fp64_fma_tflops": fp64_tflops,
         }
-        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0], grouped)
+        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0], grouped, storage, problems)
         line["roofline"]["launch_ms"] = launch_s * 1e3
         line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
         line["roofline"]["frac_of_nominal_hbm"] = achieved / HBM_NOMINAL_GBS

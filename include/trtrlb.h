@@ -249,14 +249,16 @@ int trtrlb_fp64_fma_rate(void* stream, double seconds, double* tflops);
 
 /* Kernel shape of a lattice's step (the autotuner's knobs; results do not
  * depend on them).  variant: TRTRLB_KERNEL_AUTO (the vector kernel where it
- * applies for FP32/FP16/BF16, the scalar one for FP64 and F64_DW),
+ * applies for FP32/FP16/BF16, the scalar one for FP64 and F64_DW; with
+ * G_CURRENT on a periodic lattice without a mask the TMA-fed kernel for FP32
+ * and the column kernel for FP64/FP16/BF16 from 512^2 nodes),
  * TRTRLB_KERNEL_SCALAR (one node per thread; for G_CURRENT the plain
  * two-buffer kernel instead of the TMA-fed one), TRTRLB_KERNEL_VECTOR
  * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
  * lattice is periodic in both directions, has no mask and nx is a multiple
  * of that width).
  * TRTRLB_KERNEL_COLUMN (G_CURRENT only: the two-buffer kernel whose warps walk
- * down bands of 64 rows of 30 columns, keeping the Phi of the rows above and
+ * down bands of 32 rows (16 for FP64) of 30 columns, keeping the Phi of the rows above and
  * below in registers; ENOTSUP unless the lattice is periodic in both
  * directions, has no mask and stores FP64, FP32, FP16 or BF16).
  * tile_w: width in nodes of the scalar kernel's 256-thread tile (32, 64, 128

@@ -2,7 +2,7 @@
 // periodic in x and y without a mask, walking down columns.
 //
 // The state is the canonical f(t) in buffer A, as for k_step_ab.  A warp owns
-// a band of COL_H rows and the 32 consecutive columns x0 - 1 .. x0 + 30,
+// a band of col_h rows and the 32 consecutive columns x0 - 1 .. x0 + 30,
 // x0 = COL_W * (its column group): lanes 1 .. 30 update the columns x0 ..
 // x0 + 29, lanes 0 and 31 stand on the two columns beside them.  Walking down
 // the band, every lane loads the nine populations of its column's node in the
@@ -15,15 +15,25 @@
 // (periodic wrap) as in k_step_ab.  No shared memory, no barrier: a warp needs
 // nothing from another warp, and the rows above and below a band, and the
 // columns beside a group, are loaded again by the warps that border them
-// (L2 hits; 2 of every COL_H rows and 2 of every 32 columns).
+// (L2 hits; 2 of every col_h rows and 2 of every 32 columns).  Loading the
+// row after next while a row collides (software pipelining) measured slower:
+// its registers cost a quarter of the resident warps.
 #pragma once
 #include "lb_device.cuh"
 
 namespace trt {
 
 constexpr int COL_W = 30;       // columns a warp updates
-constexpr int COL_H = 64;       // rows of a band
 constexpr int COL_WARPS = 8;    // warps per CTA
+
+// Rows of a band: shorter bands give more warps (and reload 2 rows in COL_H);
+// measured on 3 x 4096^2 (ms per step, bands of 64 / 32 / 16 rows): FP32
+// 0.712 / 0.697 / 0.703, FP16 0.547 / 0.524 / 0.522, FP64 11.66 / 11.01 /
+// 10.84.
+template <typename S>
+__host__ __device__ constexpr int col_h() {
+    return sizeof(S) == 8 ? 16 : 32;
+}
 
 // Resident CTAs per SM the column kernel asks the compiler to allow.
 template <typename S>
@@ -43,6 +53,7 @@ __global__ void __launch_bounds__(COL_WARPS * 32, col_min_blocks<S>())
     const int c = x0 + lane - 1;                      // this lane's column, unwrapped
     const int cw = (c + a.nx) % a.nx;                 // ... wrapped (x0 + 30 < 2 nx + 30)
     const bool inner = lane >= 1 && lane <= COL_W && c < a.nx;
+    constexpr int COL_H = col_h<S>();
     const int y0 = band * COL_H;
     const int y1 = y0 + COL_H < a.ny ? y0 + COL_H : a.ny;
     const S* __restrict__ F = static_cast<const S*>(a.f);

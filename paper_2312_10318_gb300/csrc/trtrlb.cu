@@ -114,6 +114,19 @@ bool auto_vector(const trtrlb_lattice* h) {
     return vector_applies(h) && st != TRTRLB_F64 && st != TRTRLB_F64_DW;
 }
 
+// Default two-buffer kernel of a G_CURRENT lattice that is periodic without a
+// mask: the column-walking kernel for FP64, FP16 and BF16 storage at 512^2
+// nodes or more (on 3 x 4096^2 it stepped FP16 in 0.551 ms against 0.696 for
+// the plain kernel, FP64 in 11.66 against 13.75); FP32 keeps the TMA-fed
+// kernel, which measured faster on one 4096^2 lattice (0.231 against
+// 0.239 ms); smaller lattices, whose bands give too few warps, the plain one.
+bool auto_column(const trtrlb_lattice* h) {
+    const int st = h->p.storage;
+    return h->p.g_mode == TRTRLB_G_CURRENT && !h->s.general &&
+           (st == TRTRLB_F64 || st == TRTRLB_F16_SHIFTED || st == TRTRLB_BF16_SHIFTED) &&
+           (long long)h->p.nx * h->p.ny >= 512ll * 512ll;
+}
+
 // Staging buffer for host transfers and comparisons: at least `fields` FP64
 // fields of nx * ny values, allocated on first use and grown when a call needs
 // more (3 for moments and init, 4 for comparisons, 11 for populations and
@@ -330,6 +343,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     s.tile_w = h->tile_w;
     h->variant = TRTRLB_KERNEL_AUTO;
     s.vec = auto_vector(h);
+    s.col = auto_column(h);
     if (p.g_mode == TRTRLB_G_CURRENT && p.storage == TRTRLB_F32 && !s.general) {
         // the TMA-fed two-buffer kernel; without a descriptor the plain one runs
         CUtensorMap* maps = new (std::nothrow) CUtensorMap[2];
@@ -667,7 +681,7 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
     }
     h->variant = variant;
     h->s.vec = vec;
-    h->s.col = variant == TRTRLB_KERNEL_COLUMN;
+    h->s.col = variant == TRTRLB_KERNEL_COLUMN || (variant == TRTRLB_KERNEL_AUTO && auto_column(h));
     // G_CURRENT: AUTO runs the TMA-fed kernel where it exists, SCALAR the plain
     // one, COLUMN the column-walking one
     h->s.tma_grid = variant == TRTRLB_KERNEL_AUTO || variant == TRTRLB_KERNEL_VECTOR ? h->tma_grid : 0;

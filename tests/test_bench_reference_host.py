@@ -82,6 +82,11 @@ def test_grouped_current_phi_launch_count():
     assert not bench.tma_grouped(a, "f32", probs * 6)          # 18 lattices: two launches
     ch = W.poiseuille(16, tau_s=0.8, magic=0.25)
     assert not bench.tma_grouped(a, "f32", [ch])                # walls in y
+    big = [W.double_shear_layer(2048, re=1e4)]
+    assert not bench.tma_grouped(a, "f32", big)                 # 2048^2 and above: a launch each
+    assert "k_step_ab_tma" in bench.kernel_label(a, False, False, "f32", big)
+    assert "k_step_ab_col" in bench.kernel_label(a, False, False, "f16", big)
+    assert "k_step_ab (" in bench.kernel_label(a, False, False, "f16", probs)   # 64^2: the plain one
 
 
 def test_reference_arm_follows_the_g_mode():

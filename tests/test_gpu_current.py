@@ -256,3 +256,40 @@ def test_column_kernel_only_where_it_applies(gpu_lib):
     ch = W.poiseuille(16, 0.8, 0.25)
     with pytest.raises(TrtrlbError):
         gpu_lattice(ch, "f32", "current").set_kernel("column")
+
+
+@pytest.mark.parametrize("storage", ["f16", "f64"])
+def test_default_current_kernel_by_size(gpu_lib, storage):
+    """With G_CURRENT on a periodic lattice without a mask the library steps
+    FP64/FP16/BF16 with the column kernel from 512^2 nodes and with the plain
+    two-buffer kernel below: the default equals the forced kernel bit for bit."""
+    for n, forced in ((512, "column"), (256, "scalar")):
+        pr = W.double_shear_layer(n, re=1e4)
+        a = gpu_lattice(pr, storage, "current").init(pr.ux, pr.uy)
+        b = gpu_lattice(pr, storage, "current").set_kernel(forced).init(pr.ux, pr.uy)
+        a.step(3)
+        b.step(3)
+        assert np.array_equal(a.get_f(), b.get_f()), (n, storage)
+
+
+def test_large_tma_lattices_take_a_launch_each_in_batches(gpu_lib):
+    """FP32 periodic current-Phi lattices of 2048^2 nodes or more do not share a
+    TMA launch in a batch: each takes the single-lattice launch, so the batch
+    equals every lattice stepped alone bit for bit."""
+    import torch
+    from paper_2312_10318_gb300.lattice import Batch
+    stream = torch.cuda.Stream()
+    pairs = []
+    for re in (1e4, 1e5):
+        pr = W.double_shear_layer(2048, re=re)
+        a = gpu_lattice(pr, "f32", "current", stream=stream).init(pr.ux, pr.uy)
+        b = gpu_lattice(pr, "f32", "current", stream=stream).init(pr.ux, pr.uy)
+        pairs.append((a, b))
+    batch = Batch(stream).set([b for _, b in pairs])
+    for n in (1, 2):
+        for a, _ in pairs:
+            a.step(n)
+        batch.step(n)
+    torch.cuda.synchronize()
+    for a, b in pairs:
+        assert np.array_equal(a.get_f(), b.get_f())
