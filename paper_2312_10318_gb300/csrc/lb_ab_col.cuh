@@ -16,8 +16,9 @@
 // nothing from another warp, and the rows above and below a band, and the
 // columns beside a group, are loaded again by the warps that border them
 // (L2 hits; 2 of every col_h rows and 2 of every 32 columns).  Loading the
-// row after next while a row collides (software pipelining) measured slower:
-// its registers cost a quarter of the resident warps.
+// row after next while a row collides (software pipelining) measured slower,
+// into registers (they cost a quarter of the resident warps) and into a
+// per-warp shared-memory ring by cp.async alike.
 #pragma once
 #include "lb_device.cuh"
 
