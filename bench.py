@@ -167,38 +167,46 @@ def kernel_source_hash(csrc: str | None = None) -> str:
     return h.hexdigest()[:16]
 
 
-# lattices below this many nodes share the TMA-fed launches of a batch (the
-# library's rule); larger ones take a launch each
-TMA_SHARE_MAX_NODES = 2048 * 2048
+# step kernels by the kind the library reports for a lattice (Lattice.step_kernel)
+KERNEL_NAMES = {
+    "aa": "trt::k_step (fused AA stream-collide)",
+    "aa_vector": "trt::k_step_vec (fused AA stream-collide)",
+    "ab": "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)",
+    "ab_tma": "trt::k_step_ab_tma (two-buffer step fed by TMA, Phi at the current level, one launch per lattice)",
+    "ab_tma_shared": "trt::k_step_ab_tma (two-buffer step fed by TMA, Phi at the current level, one launch per lattice)",
+    "ab_column": "trt::k_step_ab_col (two-buffer step walking columns, Phi at the current level, one launch per lattice)",
+}
+BATCH_KERNEL_NAMES = {
+    "aa": "trt::k_step_group (fused AA stream-collide, all lattices in one launch)",
+    "aa_vector": "trt::k_step_group_vec (fused AA stream-collide, all lattices in one launch)",
+    "ab_tma_shared": "trt::k_step_ab_tma (two-buffer step fed by TMA, Phi at the current level, "
+                     "up to 16 lattices in one launch)",
+}
+TMA_GROUP_MAX = 16      # lattices per shared TMA-fed launch
 
 
-def tma_grouped(args, storage: str, problems) -> bool:
-    """Whether a batch step of G_CURRENT lattices is one TMA-fed launch for all
-    of them (FP32, periodic, no mask, at most 16 lattices)."""
-    return (args.mode == "batch" and args.g_mode == "current" and storage == "f32" and len(problems) <= 16
-            and getattr(args, "kernel", "tuned") in ("tuned", "auto")
-            and all(p.mask is None and all(p.periodic) and p.nodes < TMA_SHARE_MAX_NODES for p in problems))
+def kernel_label(mode: str, kinds) -> str:
+    """Name of the step kernel(s) the timed region launches, from the kinds the
+    library reports for the lattices (in a batch the AA and small TMA-fed
+    lattices share launches)."""
+    names = []
+    for k in dict.fromkeys(kinds):
+        names.append(BATCH_KERNEL_NAMES.get(k, KERNEL_NAMES[k]) if mode == "batch" else KERNEL_NAMES[k])
+    return " + ".join(names)
 
 
-def kernel_label(args, vector: bool, grouped: bool = False, storage: str = "f32", problems=()) -> str:
-    """Name of the step kernel the timed region launches (the library's choice
-    for the lattice's format, G mode, boundaries and size, or the one forced)."""
-    if args.g_mode == "current":
-        if grouped:
-            return "trt::k_step_ab_tma (two-buffer step, Phi at the current level, all lattices in one launch)"
-        plain_periodic = all(p.mask is None and all(p.periodic) for p in problems)
-        k = getattr(args, "kernel", "tuned")
-        auto = k in ("tuned", "auto")
-        if k == "column" or (auto and plain_periodic and storage in ("f64", "f16", "bf16")
-                             and all(p.nodes >= 512 * 512 for p in problems)):
-            return "trt::k_step_ab_col (two-buffer step walking columns, Phi at the current level, one launch per lattice)"
-        if auto and plain_periodic and storage == "f32":
-            return "trt::k_step_ab_tma (two-buffer step fed by TMA, Phi at the current level, one launch per lattice)"
-        return "trt::k_step_ab (two-buffer step, Phi at the current level, one launch per lattice)"
-    if args.mode == "batch":
-        return ("trt::k_step_group_vec" if vector else "trt::k_step_group") + \
-            " (fused AA stream-collide, all lattices in one launch)"
-    return ("trt::k_step_vec" if vector else "trt::k_step") + " (fused AA stream-collide)"
+def step_launches(mode: str, kinds) -> int:
+    """Step-kernel launches per time step: one per lattice outside a batch; in a
+    batch one per AA kernel kind (the benchmark's lattices share format, boundary
+    flavour and parity), one per TMA_GROUP_MAX lattices that share TMA-fed
+    launches, and one per other two-buffer lattice."""
+    kinds = list(kinds)
+    if mode != "batch":
+        return len(kinds)
+    aa = {k for k in kinds if k in ("aa", "aa_vector")}
+    shared = sum(k == "ab_tma_shared" for k in kinds)
+    alone = sum(k in ("ab", "ab_tma", "ab_column") for k in kinds)
+    return len(aa) + -(-shared // TMA_GROUP_MAX) + alone
 
 
 def recorded_traffic(workload_name: str):
@@ -549,8 +557,7 @@ def main():
         lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, g_mode=args.g_mode, stream=stream,
                       **pr.lattice_kwargs())
         if args.kernel == "tuned":
-            if args.g_mode != "current":     # the two-buffer kernel has one shape
-                tuner.apply(lat, pr.periodic, pr.mask is not None)
+            tuner.apply(lat, pr.periodic, pr.mask is not None)
         else:
             lat.set_kernel(args.kernel, args.tile_w)
         lat.init(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
@@ -628,9 +635,8 @@ def main():
     fp64_tflops = fp64_fma_rate(stream)
 
     # roofline of the step kernel: algorithmic bytes per launch / mean launch time
-    # the two-buffer (current-Phi) kernel runs one launch per lattice in a batch
-    grouped = tma_grouped(args, storage, problems)
-    per_step_launches = 1 if (args.mode == "batch" and (args.g_mode != "current" or grouped)) else len(lats)
+    kinds = [lat.step_kernel() for lat in lats]
+    per_step_launches = step_launches(args.mode, kinds)
     launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
     per_launch_bytes = bytes_per_node(storage, args.g_mode) * nodes / per_step_launches
@@ -695,7 +701,7 @@ def main():
             "clocks": clk,
             "fp64_fma_tflops": fp64_tflops,
         }
-        line["roofline"]["kernel"] = kernel_label(args, lats[0].kernel()[0], grouped, storage, problems)
+        line["roofline"]["kernel"] = kernel_label(args.mode, kinds)
         line["roofline"]["launch_ms"] = launch_s * 1e3
         line["roofline"]["hbm_gbs"] = achieved        # algorithmic bytes / time, every format
         line["roofline"]["frac_of_nominal_hbm"] = achieved / HBM_NOMINAL_GBS

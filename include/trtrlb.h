@@ -295,6 +295,28 @@ int trtrlb_set_wait_limit(trtrlb_t h, int64_t polls);
  * Either pointer may be NULL. */
 int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w);
 
+/* Which step kernel the lattice's current settings select (format, G mode,
+ * boundaries, size and trtrlb_set_kernel), as *kind:
+ *   TRTRLB_STEP_AA            fused AA stream-collide, one node per thread
+ *                             (k_step; in a batch k_step_group)
+ *   TRTRLB_STEP_AA_VECTOR     the same, a vector of nodes per thread
+ *   TRTRLB_STEP_AB            two-buffer step with Phi at the current level,
+ *                             one node per thread
+ *   TRTRLB_STEP_AB_TMA        two-buffer step fed by TMA, one launch for this
+ *                             lattice, in a batch too
+ *   TRTRLB_STEP_AB_TMA_SHARED the same kernel; in a batch it shares launches
+ *                             (up to 16 lattices each) with the other such
+ *                             members
+ *   TRTRLB_STEP_AB_COLUMN     two-buffer step walking columns.
+ * Host only, no device work.  EINVAL for a null handle or output. */
+#define TRTRLB_STEP_AA 0
+#define TRTRLB_STEP_AA_VECTOR 1
+#define TRTRLB_STEP_AB 2
+#define TRTRLB_STEP_AB_TMA 3
+#define TRTRLB_STEP_AB_TMA_SHARED 4
+#define TRTRLB_STEP_AB_COLUMN 5
+int trtrlb_step_kernel(trtrlb_t h, int32_t* kind);
+
 /* ---- slab decomposition -----------------------------------------------------
  * One lattice split into nslabs sub-lattices of consecutive rows (y), the
  * single-device form of a multi-GPU domain split (the paper has none; its

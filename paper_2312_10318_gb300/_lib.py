@@ -16,6 +16,8 @@ F64, F32, F16_SHIFTED, BF16_SHIFTED, F64_DW = 0, 1, 2, 3, 4
 G_LAGGED, G_CURRENT, G_OFF = 0, 1, 2
 FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_COLUMN = 0, 1, 2, 3
+# trtrlb_step_kernel kinds, by position
+STEP_KINDS = ("aa", "aa_vector", "ab", "ab_tma", "ab_tma_shared", "ab_column")
 CMP_N = 10      # outputs of trtrlb_compare / trtrlb_compare_lattices
 
 # every function the header declares, with (restype, argtypes)
@@ -55,6 +57,7 @@ SIGNATURES = {
     "trtrlb_device_bytes": (C.c_int64, [_vp]),
     "trtrlb_set_kernel": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "trtrlb_get_kernel": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "trtrlb_step_kernel": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "trtrlb_set_wait_limit": (C.c_int, [_vp, _i64]),
     "trtrlb_state_bytes": (C.c_int64, [_vp]),
     "trtrlb_save": (C.c_int, [_vp, _vp]),

@@ -18,17 +18,6 @@
 
 namespace {
 
-// Lattices below this many nodes share the TMA-fed two-buffer launches of a
-// batch (one persistent grid, one tail: 3 x 1024^2 FP32 54.2 -> 56.6 GLUPS);
-// larger ones take a launch each (one 4096^2 lattice steps alone in 0.231 ms,
-// three of them sharing a launch in 0.90 ms).
-constexpr long long kTmaShareMaxNodes = 2048ll * 2048ll;
-
-bool shares_tma_launch(const trtrlb_lattice* h) {
-    return h->s.g_mode == TRTRLB_G_CURRENT && h->p.storage == TRTRLB_F32 &&
-           trt::Ops<float>::tma_eligible(h->s) && (long long)h->p.nx * h->p.ny < kTmaShareMaxNodes;
-}
-
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity and Phi
                                  // buffers return to their start after a replay)
 

@@ -704,6 +704,19 @@ int trtrlb_get_kernel(trtrlb_t h, int32_t* vector, int32_t* tile_w) {
     return TRTRLB_OK;
 }
 
+int trtrlb_step_kernel(trtrlb_t h, int32_t* kind) {
+    if (!h || !kind) return TRTRLB_EINVAL;
+    if (h->p.g_mode != TRTRLB_G_CURRENT)
+        *kind = h->s.vec ? TRTRLB_STEP_AA_VECTOR : TRTRLB_STEP_AA;
+    else if (h->p.storage == TRTRLB_F32 && trt::Ops<float>::tma_eligible(h->s))
+        *kind = shares_tma_launch(h) ? TRTRLB_STEP_AB_TMA_SHARED : TRTRLB_STEP_AB_TMA;
+    else if (h->s.col && !h->s.general && h->p.storage != TRTRLB_F64_DW)
+        *kind = TRTRLB_STEP_AB_COLUMN;
+    else
+        *kind = TRTRLB_STEP_AB;
+    return TRTRLB_OK;
+}
+
 const char* trtrlb_strerror(int code) {
     switch (code) {
         case TRTRLB_OK: return "ok";

@@ -81,6 +81,7 @@ class Lattice:
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.g_mode = G_MODE[g_mode] if isinstance(g_mode, str) else int(g_mode)
         self.nx, self.ny, self.storage = p.nx, p.ny, storage
+        self.g_mode = next((k for k, v in G_MODE.items() if v == p.g_mode), str(p.g_mode))
         m = None
         if mask is not None:
             m = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -175,6 +176,15 @@ class Lattice:
         vec, tw = C.c_int32(), C.c_int32()
         self._chk(self._lib.trtrlb_get_kernel(self._h, C.byref(vec), C.byref(tw)))
         return bool(vec.value), tw.value
+
+    def step_kernel(self) -> str:
+        """The step kernel the current settings select: 'aa' | 'aa_vector' (fused
+        AA stream-collide), 'ab' | 'ab_tma' | 'ab_tma_shared' | 'ab_column'
+        (two-buffer step with Phi at the current level; 'ab_tma_shared' shares
+        its launches with other such lattices in a Batch)."""
+        k = C.c_int32()
+        self._chk(self._lib.trtrlb_step_kernel(self._h, C.byref(k)))
+        return _lib.STEP_KINDS[k.value]
 
     def init(self, ux, uy, rho=None):
         """Initial state from (rho, u) (rho None: rho0)."""
@@ -309,6 +319,7 @@ class Slabs:
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.g_mode = G_MODE[g_mode] if isinstance(g_mode, str) else int(g_mode)
         self.nx, self.ny, self.storage = p.nx, p.ny, storage
+        self.g_mode = next((k for k, v in G_MODE.items() if v == p.g_mode), str(p.g_mode))
         m = None
         if mask is not None:
             m = np.ascontiguousarray(mask, dtype=np.uint8)

@@ -64,29 +64,29 @@ def test_cpu_baseline_reports_all_cores_and_one_core():
     assert cb["one_core"]["value"] > 0 and cb["cpu_model"]
 
 
-def test_grouped_current_phi_launch_count():
-    """A batch of FP32 periodic current-Phi lattices (at most 16) is one
-    TMA-fed launch per step; other formats, masks, open edges or single mode
-    keep one launch per lattice (the roofline divides by the launches)."""
-    import argparse
+def test_launch_count_and_label_follow_the_reported_kernels():
+    """The roofline divides by the step-kernel launches per time step, counted
+    from the kernels the library reports: in a batch the AA lattices share a
+    launch, the small TMA-fed ones share one per 16, every other two-buffer
+    lattice takes its own; outside a batch every lattice is a launch."""
     sys.path.insert(0, ROOT)
     import bench
-    from paper_2312_10318_gb300 import workloads as W
-    probs = [W.double_shear_layer(64, re=1e4) for _ in range(3)]
-    a = argparse.Namespace(mode="batch", g_mode="current")
-    assert bench.tma_grouped(a, "f32", probs)
-    assert "all lattices in one launch" in bench.kernel_label(a, False, True)
-    assert not bench.tma_grouped(a, "f16", probs)
-    assert not bench.tma_grouped(argparse.Namespace(mode="single", g_mode="current"), "f32", probs)
-    assert not bench.tma_grouped(argparse.Namespace(mode="batch", g_mode="lagged"), "f32", probs)
-    assert not bench.tma_grouped(a, "f32", probs * 6)          # 18 lattices: two launches
-    ch = W.poiseuille(16, tau_s=0.8, magic=0.25)
-    assert not bench.tma_grouped(a, "f32", [ch])                # walls in y
-    big = [W.double_shear_layer(2048, re=1e4)]
-    assert not bench.tma_grouped(a, "f32", big)                 # 2048^2 and above: a launch each
-    assert "k_step_ab_tma" in bench.kernel_label(a, False, False, "f32", big)
-    assert "k_step_ab_col" in bench.kernel_label(a, False, False, "f16", big)
-    assert "k_step_ab (" in bench.kernel_label(a, False, False, "f16", probs)   # 64^2: the plain one
+    from paper_2312_10318_gb300 import _lib
+    assert set(bench.KERNEL_NAMES) == set(_lib.STEP_KINDS)
+    assert bench.step_launches("batch", ["aa"] * 3) == 1
+    assert bench.step_launches("batch", ["aa_vector"] * 3) == 1
+    assert bench.step_launches("single", ["aa"] * 3) == 3
+    assert bench.step_launches("batch", ["ab_tma_shared"] * 3) == 1
+    assert bench.step_launches("batch", ["ab_tma_shared"] * 18) == 2     # 16 + 2
+    assert bench.step_launches("batch", ["ab_tma"] * 3) == 3             # 4096^2: a launch each
+    assert bench.step_launches("batch", ["ab_column"] * 3 + ["ab"]) == 4
+    assert bench.step_launches("single", ["ab_tma_shared"] * 3) == 3
+    assert "up to 16 lattices in one launch" in bench.kernel_label("batch", ["ab_tma_shared"] * 3)
+    assert "one launch per lattice" in bench.kernel_label("single", ["ab_tma_shared"])
+    assert bench.kernel_label("batch", ["aa_vector"] * 3).startswith("trt::k_step_group_vec ")
+    assert bench.kernel_label("single", ["aa"]).startswith("trt::k_step ")
+    assert "k_step_ab_col" in bench.kernel_label("batch", ["ab_column"] * 3)
+    assert bench.kernel_label("batch", ["ab_column", "ab"]).count("+") == 1
 
 
 def test_reference_arm_follows_the_g_mode():

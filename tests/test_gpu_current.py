@@ -205,8 +205,8 @@ def test_tma_wait_that_runs_out_is_reported(gpu_lib):
                                    (30, 64), (31, 65)])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_column_kernel_matches_oracle(gpu_lib, nx, ny, storage):
-    """The column-walking two-buffer kernel (warps walking bands of 64 rows of
-    30 columns; lanes beside the group give the neighbours' Phi by shuffle, the
+    """The column-walking two-buffer kernel (warps walking bands of 32 rows, 16
+    in FP64, of 30 columns; lanes beside the group give the neighbours' Phi by shuffle, the
     rows above and below are kept from the walk) against the oracle's CURRENT
     mode on periodic lattices of sizes that leave partial groups and bands,
     wrap within one group, or have one row or column: FP64 to 1e-12 per field,
@@ -293,3 +293,22 @@ def test_large_tma_lattices_take_a_launch_each_in_batches(gpu_lib):
     torch.cuda.synchronize()
     for a, b in pairs:
         assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_reported_step_kernel(gpu_lib):
+    """trtrlb_step_kernel names the kernel the settings select: the AA kernels
+    with Phi lagged, and with Phi at the current level the TMA-fed kernel for
+    FP32 (shared launches below 2048^2 nodes), the column kernel for FP16 from
+    512^2, the plain one otherwise (walls, small lattices, or forced)."""
+    dsl = {n: W.double_shear_layer(n, re=1e4) for n in (256, 512, 2048)}
+    assert gpu_lattice(dsl[256], "f32", "lagged").step_kernel() == "aa_vector"
+    assert gpu_lattice(dsl[256], "f32", "lagged").set_kernel("scalar").step_kernel() == "aa"
+    assert gpu_lattice(dsl[256], "f32", "current").step_kernel() == "ab_tma_shared"
+    assert gpu_lattice(dsl[2048], "f32", "current").step_kernel() == "ab_tma"
+    assert gpu_lattice(dsl[256], "f32", "current").set_kernel("scalar").step_kernel() == "ab"
+    assert gpu_lattice(dsl[256], "f32", "current").set_kernel("column").step_kernel() == "ab_column"
+    assert gpu_lattice(dsl[512], "f16", "current").step_kernel() == "ab_column"
+    assert gpu_lattice(dsl[256], "f16", "current").step_kernel() == "ab"
+    assert gpu_lattice(dsl[512], "f64dw", "current").step_kernel() == "ab"
+    ch = W.poiseuille(16, 0.8, 0.25)
+    assert gpu_lattice(ch, "f32", "current").step_kernel() == "ab"

@@ -33,3 +33,26 @@ def test_tuner_measures_caches_and_applies(gpu_lib, tmp_path):
     for lat in (a, b):
         lat.init(pr.ux, pr.uy, pr.rho).step(37)
     assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_tuner_chooses_among_current_phi_kernels(gpu_lib, tmp_path):
+    """With Phi at the current level the tuner times the plain, column and (FP32)
+    TMA-fed two-buffer kernels and applies the fastest: the lattice then steps
+    with that kernel, bit for bit as when it is forced."""
+    from paper_2312_10318_gb300 import Lattice
+    t = T.Tuner(cache_path=str(tmp_path / "tune.json"), steps=16, reps=2)
+    kind = {"scalar": "ab", "auto": "ab_tma_shared", "column": "ab_column"}
+    for storage in ("f32", "f16"):
+        n = 512
+        v, tw = t.choose(storage, n, n, g_mode="current")
+        cands = t.candidates(storage, n, (True, True), False, "current")
+        assert (v, tw) in cands
+        assert set(t.measured[f"{storage}/periodic/current/{n}x{n}"]) == {f"{a}:{b}" for a, b in cands}
+        pr = W.double_shear_layer(n, re=1e4)
+        a = Lattice(n, n, pr.tau_s, storage=storage, g_mode="current", **pr.lattice_kwargs())
+        t.apply(a, pr.periodic)
+        assert a.step_kernel() == kind[v]
+        b = Lattice(n, n, pr.tau_s, storage=storage, g_mode="current", **pr.lattice_kwargs()).set_kernel(v)
+        for lat in (a, b):
+            lat.init(pr.ux, pr.uy).step(5)
+        assert np.array_equal(a.get_f(), b.get_f()), storage
