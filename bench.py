@@ -676,12 +676,13 @@ def main():
             "config": {"workload": desc, "lattices": len(problems), "nx": problems[0].nx,
                        "ny": problems[0].ny, "nodes_per_step": nodes, "storage": storage,
                        "g_mode": args.g_mode,
-                       "kernel": ("vector" if lats[0].kernel()[0] else f"scalar, tile {lats[0].kernel()[1]}")
+                       "kernel": ", ".join(dict.fromkeys(
+                           k + (f", tile {lat.kernel()[1]}" if k == "aa" else "") for k, lat in zip(kinds, lats)))
                                  + (" (autotuned)" if args.kernel == "tuned" else ""),
                        "tuning": tuner.measured if args.kernel == "tuned" else None,
                        "parallelism": f"replicas x{world}",
-                       "launch": "one batched kernel per time step" if args.mode == "batch"
-                                 else "one kernel per lattice and time step",
+                       "launch": (f"{per_step_launches} step-kernel launch(es) per time step, "
+                                  + ("batched" if args.mode == "batch" else "one lattice each")),
                        "working_set_bytes": working_set,
                        "l2": ("inputs larger than L2: the timed steps run back to back, no flush "
                               f"(working set {working_set / 1e9:.2f} GB against a 129 MB L2)"

@@ -134,7 +134,9 @@ int trtrlb_create(const trtrlb_params* p, const uint8_t* mask, void* stream, trt
 /* Frees all memory of the handle (synchronises its stream).  NULL is a no-op. */
 int trtrlb_destroy(trtrlb_t h);
 
-/* Changes the stream later work is ordered on. */
+/* Changes the stream later work is ordered on.  Work already queued on the
+ * old stream is not waited for: the caller orders the two streams (an event
+ * recorded on the old one and waited for on the new one). */
 int trtrlb_set_stream(trtrlb_t h, void* stream);
 
 /* Initial state from macroscopic fields (t = 0):

@@ -94,7 +94,7 @@ int check_kerr(trtrlb_lattice* h) {
     int v = 0;
     if (cudaMemcpy(&v, h->kerr, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return TRTRLB_ECUDA;
     if (!v) return TRTRLB_OK;
-    cudaMemset(h->kerr, 0, sizeof v);
+    cudaMemsetAsync(h->kerr, 0, sizeof v, h->stream);
     return fail(h->err, TRTRLB_ETIMEOUT, "a step kernel's wait for its tile copy ran out");
 }
 
@@ -348,7 +348,8 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
         // the TMA-fed two-buffer kernel; without a descriptor the plain one runs
         CUtensorMap* maps = new (std::nothrow) CUtensorMap[2];
         e = maps ? cudaMalloc((void**)&h->kerr, sizeof(int)) : cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) e = cudaMemset(h->kerr, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess) e = encode_tma(h->f, p.nx, p.ny, pitch, &maps[0]);
         if (e == cudaSuccess) e = encode_tma(h->f2, p.nx, p.ny, pitch, &maps[1]);
         if (e == cudaSuccess) {

@@ -219,6 +219,13 @@ class PrecisionGuard:
         self.probe = probe
         self.fp64 = fp64
         self.checked = []      # (rid, storage, e_end, predicted, tol)
+        # callable(lattice) that disposes of the probe lattices the check does
+        # not keep (default: close at once; a Server defers it to a point where
+        # freeing device memory does not wait for the kernels in flight)
+        self.release = None
+
+    def _release(self, lat):
+        (self.release or (lambda L: L.close()))(lat)
 
     @staticmethod
     def _err(a, b, scale: float) -> float:
@@ -259,14 +266,14 @@ class PrecisionGuard:
                 break
             storage = WIDER[storage]
             if cur is not lat:
-                cur.close()
+                self._release(cur)
             if storage != "f64":
                 cur = init(make(storage))
         if storage == "f64":
             if cur is not lat and cur is not shadow:
-                cur.close()
+                self._release(cur)
             return init(shadow)
-        shadow.close()
+        self._release(shadow)
         return init(cur)
 
     def __call__(self, req: Request, lat):
@@ -323,6 +330,9 @@ class Server:
     lattices hold this many nodes (the GPU is bandwidth-saturated well below
     it), so requests finish closer to arrival order.  tuner: optional
     tune.Tuner whose kernel shapes are applied to every admitted lattice.
+    defer_bytes: device bytes of released lattices (retired, or probes of the
+    precision guard) whose freeing may wait for the end of the chunk in flight;
+    above it they are freed at once, which waits for the chunk.
     fp64_as: "f64dw" runs FP64 requests in the 64-bit double-word format (FP32
     pairs, ~48-bit arithmetic; agrees with FP64 within the FP64 parity
     tolerance and runs ~4x faster on GB300), "f64" in native FP64."""
@@ -330,11 +340,16 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, chunk: int = 512, check_every: int = 8,
                  guard: Optional[Callable] = None, max_u: float = 0.5, stream=None,
                  on_retire: Optional[Callable] = None, max_active_nodes: float = 48e6,
-                 tuner=None, fp64_as: str = "f64"):
+                 tuner=None, fp64_as: str = "f64", defer_bytes: float = 16e9):
         import torch
         from .lattice import Batch
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        # admission (lattice set-up and the guard's probes) runs on its own
+        # stream, beside the chunk in flight on self.stream
+        self.admit_stream = torch.cuda.Stream()
         self.batch = Batch(self.stream)
+        self.defer_bytes = float(defer_bytes)
+        self._deferred = []            # lattices to free after the chunk in flight
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
         self.check_every = int(check_every)
@@ -347,6 +362,8 @@ class Server:
         self._cancelled = set()       # request ids to drop (see cancel)
         if guard is not None and hasattr(guard, "fp64"):
             guard.fp64 = fp64_as      # the guard's shadow and last fallback use it too
+        if guard is not None and hasattr(guard, "release"):
+            guard.release = self._release
         self.active_nodes = 0
         self.used = 0
         self.node_updates = 0
@@ -364,10 +381,11 @@ class Server:
         if self.active_nodes > 0 and self.active_nodes + req.n * req.n > self.max_active_nodes:
             return None
         pr = spec_of(req)
-        # fields and init on the server's stream: the fields' memory is then
-        # stream-ordered with the kernels that read it
-        with torch.cuda.stream(self.stream):
-            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, stream=self.stream,
+        # fields, init and the guard's probes on the admission stream: the
+        # fields' memory is stream-ordered with the kernels that read it, and
+        # the work runs beside the chunk in flight
+        with torch.cuda.stream(self.admit_stream):
+            lat = Lattice(pr.nx, pr.ny, pr.tau_s, storage=storage, stream=self.admit_stream,
                           **pr.lattice_kwargs())
             ux, uy, rho = device_fields(req, pr)
             lat.init(ux, uy, rho)
@@ -378,7 +396,7 @@ class Server:
                     act.fallback = True
                     act.storage = lat2.storage
                     act.nbytes = lattice_bytes(req.n, req.n, lat2.storage)
-                    lat.close()
+                    self._release(lat)
                     act.lat = lat2
             if self.tuner is not None:
                 self.tuner.apply(act.lat, pr.periodic)
@@ -389,11 +407,24 @@ class Server:
     def _retire(self, a: _Active, now: float, status: str, diag: dict) -> Result:
         if self.on_retire is not None:
             self.on_retire(a.req, a.lat, status)
-        a.lat.close()
+        self._release(a.lat)
         self.used -= a.nbytes
         self.active_nodes -= a.req.n * a.req.n
         return Result(a.req.rid, status, a.storage, a.req.steps - a.remaining, diag, a.req.arrival,
                       a.t_admit, now, a.fallback)
+
+    def _release(self, lat):
+        """Frees a lattice's device memory once nothing in flight can use it:
+        cudaFree waits for every kernel on the device, so the memory of lattices
+        released while a chunk runs is freed after the chunk."""
+        self._deferred.append(lat)
+        if sum(L.device_bytes() for L in self._deferred) > self.defer_bytes:
+            self._flush()
+
+    def _flush(self):
+        for L in self._deferred:
+            L.close()
+        self._deferred = []
 
     def cancel(self, rid: int):
         """Drops request `rid`: a waiting one never starts; an active one is
@@ -406,12 +437,21 @@ class Server:
         return d["nonfinite"] > 0 or not math.isfinite(d["max_u"]) or d["max_u"] > self.max_u
 
     def run(self, requests: list, realtime: bool = True) -> list:
-        """Serves the stream; with realtime=False every request is available at once."""
+        """Serves the stream; with realtime=False every request is available at once.
+
+        One scheduling point per chunk.  The chunk's steps are launched for the
+        active lattices; while the GPU runs them the host admits waiting
+        requests (their lattices are made, initialised and checked by the
+        precision guard on the admission stream, so that work shares the GPU
+        with the chunk), then waits for the chunk, retires the solves that are
+        done, frees what was released, and adds the admitted lattices to the
+        next chunk."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting, active, results = [], [], []
         members = None
         chunks = 0
+        in_flight = 0          # steps of the chunk launched and not yet waited for
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
         while pending or waiting or active:
@@ -421,7 +461,8 @@ class Server:
             for req in [r for r in waiting if r.rid in self._cancelled]:
                 waiting.remove(req)
                 results.append(Result(req.rid, "cancelled", req.storage, 0, {}, req.arrival, now, now))
-            # admission, first come first served
+            # admission, first come first served, beside the chunk in flight
+            admitted = []
             while waiting:
                 req = waiting[0]
                 if lattice_bytes(req.n, req.n, self.fp64_as if req.storage == "f64" else req.storage) > self.budget:
@@ -432,9 +473,46 @@ class Server:
                 if a is None:
                     break
                 waiting.pop(0)
-                active.append(a)
+                admitted.append(a)
+            if in_flight:
+                self.stream.synchronize()
+                n, in_flight = in_flight, 0
+                chunks += 1
+                self.node_updates += n * sum(a.req.n * a.req.n for a in active)
+                for a in active:
+                    a.remaining -= n
+                now = clock()
+                check = self.check_every > 0 and chunks % self.check_every == 0
+                keep = []
+                for a in active:
+                    if a.req.rid in self._cancelled and a.remaining > 0:
+                        results.append(self._retire(a, now, "cancelled", a.lat.diagnostics()))
+                        continue
+                    if a.remaining == 0 or check:
+                        d = a.lat.diagnostics()
+                        if self._unstable(d):
+                            results.append(self._retire(a, now, "unstable", d))
+                            continue
+                        if a.remaining == 0:
+                            results.append(self._retire(a, now, "ok", d))
+                            continue
+                    keep.append(a)
+                active = keep
+            if admitted:
+                # the batch's stream takes over the admitted lattices after the
+                # admission stream's work on them
+                ev = torch.cuda.Event()
+                ev.record(self.admit_stream)
+                self.stream.wait_event(ev)
+                for a in admitted:
+                    a.lat.set_stream(self.stream)
+                active.extend(admitted)
+            self._flush()          # nothing in flight: freeing waits for no kernel
             if not active:
-                if pending:
+                if members:
+                    self.batch.set([])
+                    members = None
+                if pending and not waiting:
                     time.sleep(max(0.0, min(0.05, pending[0].arrival - clock())))
                 continue
             lats = [a.lat for a in active]
@@ -443,32 +521,7 @@ class Server:
                 members = lats
             n = min(self.chunk, min(a.remaining for a in active))
             self.batch.step(n)
-            self.stream.synchronize()
-            chunks += 1
-            self.node_updates += n * sum(a.req.n * a.req.n for a in active)
-            for a in active:
-                a.remaining -= n
-            now = clock()
-            check = self.check_every > 0 and chunks % self.check_every == 0
-            keep = []
-            for a in active:
-                if a.req.rid in self._cancelled and a.remaining > 0:
-                    results.append(self._retire(a, now, "cancelled", a.lat.diagnostics()))
-                    continue
-                if a.remaining == 0 or check:
-                    d = a.lat.diagnostics()
-                    if self._unstable(d):
-                        results.append(self._retire(a, now, "unstable", d))
-                        continue
-                    if a.remaining == 0:
-                        results.append(self._retire(a, now, "ok", d))
-                        continue
-                keep.append(a)
-            if len(keep) != len(active):
-                active = keep
-                members = None
-                if not active:
-                    self.batch.set([])
+            in_flight = n
         self.makespan = clock()
         return sorted(results, key=lambda r: r.rid)
 
