@@ -253,16 +253,19 @@ int trtrlb_fp64_fma_rate(void* stream, double seconds, double* tflops);
  * depend on them).  variant: TRTRLB_KERNEL_AUTO (the vector kernel where it
  * applies for FP32/FP16/BF16, the scalar one for FP64 and F64_DW; with
  * G_CURRENT on a periodic lattice without a mask the TMA-fed kernel for FP32
- * and the column kernel for FP64/FP16/BF16 from 512^2 nodes),
+ * and the column kernel for FP64/FP16/BF16 where its bands give at least
+ * half as many warps as the device holds resident -- on 152 SMs from 1024^2
+ * nodes for FP16/BF16 and 512^2 for FP64 --, the plain one below),
  * TRTRLB_KERNEL_SCALAR (one node per thread; for G_CURRENT the plain
  * two-buffer kernel instead of the TMA-fed one), TRTRLB_KERNEL_VECTOR
  * (a vector of nodes per thread: 2 for FP64, 4 otherwise; ENOTSUP unless the
  * lattice is periodic in both directions, has no mask and nx is a multiple
  * of that width).
  * TRTRLB_KERNEL_COLUMN (G_CURRENT only: the two-buffer kernel whose warps walk
- * down bands of 32 rows (16 for FP64) of 30 columns, keeping the Phi of the rows above and
- * below in registers; ENOTSUP unless the lattice is periodic in both
- * directions, has no mask and stores FP64, FP32, FP16 or BF16).
+ * down bands of rows of 30 columns, keeping the Phi of the rows above and
+ * below in registers; bands of 32, 16 or 8 rows (FP64: 16, 8 or 4), the
+ * tallest that fills the device; ENOTSUP unless the lattice is periodic in
+ * both directions, has no mask and stores FP64, FP32, FP16 or BF16).
  * tile_w: width in nodes of the scalar kernel's 256-thread tile (32, 64, 128
  * or 256; 0 keeps the current one). */
 #define TRTRLB_KERNEL_AUTO 0
@@ -382,6 +385,24 @@ int trtrlb_batch_set(trtrlb_batch_t b, const trtrlb_t* lattices, int count);
 
 /* Advances every member by nsteps >= 0 steps (asynchronous). */
 int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps);
+
+/* End-to-end solve of every member: member k starts from the fields
+ * (rho[k], ux[k], uy[k]) as trtrlb_init does (eq11 moments; rho[k], or the
+ * array rho itself, NULL for rho0), advances nsteps >= 0 time steps, and its
+ * eq11 moments are written to rho_out[k], ux_out[k], uy_out[k] (each, or each
+ * array, may be NULL).  Arrays are [ny][nx] doubles in host or device memory;
+ * host arrays should be page-locked for the copies to run beside the steps.
+ * The members advance one after another, each with its own launches (as
+ * trtrlb_step), so that the upload of the next member and the download of
+ * the previous one run on two copy streams of the batch while a member
+ * steps; the results equal trtrlb_init, trtrlb_step and trtrlb_moments of
+ * each member alone.  Ordered after the work already queued on the members'
+ * streams and on the batch's stream; returns when the outputs are written.
+ * EINVAL for a bad argument, ECUDA for a CUDA error, ETIMEOUT as
+ * trtrlb_moments. */
+int trtrlb_batch_solve(trtrlb_batch_t b, const double* const* rho, const double* const* ux,
+                       const double* const* uy, int64_t nsteps, double* const* rho_out,
+                       double* const* ux_out, double* const* uy_out);
 
 /* Frees the batch (not its lattices); synchronises its stream. */
 int trtrlb_batch_destroy(trtrlb_batch_t b);

@@ -65,6 +65,8 @@ SIGNATURES = {
     "trtrlb_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "trtrlb_batch_set": (C.c_int, [_vp, C.POINTER(_vp), C.c_int]),
     "trtrlb_batch_step": (C.c_int, [_vp, _i64]),
+    "trtrlb_batch_solve": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _i64,
+                                     C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
     "trtrlb_batch_destroy": (C.c_int, [_vp]),
     "trtrlb_batch_last_error": (C.c_char_p, [_vp]),
     "trtrlb_slabs_create": (C.c_int, [C.POINTER(Params), _vp, C.c_int32, _vp, C.POINTER(_vp)]),

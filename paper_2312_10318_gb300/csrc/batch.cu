@@ -25,6 +25,8 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity and P
 
 struct trtrlb_batch {
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_in = nullptr;    // uploads and downloads of trtrlb_batch_solve
+    cudaStream_t copy_out = nullptr;   // (created on its first call)
     std::vector<trtrlb_t> lats;
     cudaGraphExec_t graph = nullptr;
     std::vector<int> graph_sig;   // (parity, cur) of every member when captured
@@ -167,6 +169,8 @@ int trtrlb_batch_destroy(trtrlb_batch_t b) {
     if (!b) return TRTRLB_OK;
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    if (b->copy_in) cudaStreamDestroy(b->copy_in);
+    if (b->copy_out) cudaStreamDestroy(b->copy_out);
     delete b;
     return TRTRLB_OK;
 }
@@ -184,6 +188,19 @@ int trtrlb_batch_set(trtrlb_batch_t b, const trtrlb_t* lattices, int count) {
     drop_graph(b);
     b->lats.swap(l);
     return TRTRLB_OK;
+}
+
+int trtrlb_batch_solve(trtrlb_batch_t b, const double* const* rho, const double* const* ux,
+                       const double* const* uy, int64_t nsteps, double* const* rho_out,
+                       double* const* ux_out, double* const* uy_out) {
+    if (!b) return TRTRLB_EINVAL;
+    b->err[0] = 0;
+    cudaError_t e = cudaSuccess;
+    if (!b->copy_in) e = cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !b->copy_out) e = cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(b, e, "copy streams");
+    return trt::solve_members(b->lats.data(), (int)b->lats.size(), b->stream, b->copy_in, b->copy_out, rho, ux,
+                              uy, nsteps, rho_out, ux_out, uy_out, b->err);
 }
 
 int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps) {

@@ -26,6 +26,7 @@ struct trtrlb_lattice {
     void* tmaps;         // two CUtensorMap (host) of the FP32 periodic G_CURRENT kernel, or null
     int* kerr;           // device flag set when a kernel's bounded wait ran out, or null
     int tma_grid;        // persistent grid of the TMA kernel on this device (0: none)
+    int sms;             // multiprocessors of the handle's device
     char err[256];
 };
 
@@ -39,3 +40,11 @@ inline bool shares_tma_launch(const trtrlb_lattice* h) {
     return h->s.g_mode == TRTRLB_G_CURRENT && h->p.storage == TRTRLB_F32 &&
            trt::Ops<float>::tma_eligible(h->s) && (long long)h->p.nx * h->p.ny < kTmaShareMaxNodes;
 }
+
+namespace trt {
+// Body of trtrlb_batch_solve over the members m[0 .. count): see trtrlb.h.
+// st runs the members' kernels; cin and cout their uploads and downloads.
+int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t cin, cudaStream_t cout,
+                  const double* const* rho, const double* const* ux, const double* const* uy, int64_t nsteps,
+                  double* const* rho_out, double* const* ux_out, double* const* uy_out, char* err);
+}  // namespace trt

@@ -44,7 +44,8 @@ struct State {
     int px, py;
     bool general;         // walls, mask or non-periodic edges present
     bool vec;             // the vectorised kernel runs this lattice
-    bool col;             // G_CURRENT: the column-walking two-buffer kernel runs it
+    int col_h;            // G_CURRENT: rows per band of the column-walking two-buffer
+                          // kernel, which runs the step; 0: another kernel
     int tile_w;           // scalar kernels: block of tile_w x (256 / tile_w) nodes
     int g_mode;
     double tau1, tau2, gx, gy, rho0;

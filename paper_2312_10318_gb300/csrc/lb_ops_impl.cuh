@@ -84,11 +84,11 @@ cudaError_t Ops<S>::step_ab(const State& s, int q, cudaStream_t st) {
     }
     const Args<C> a = make_args<C>(v);
     if constexpr (!std::is_same<S, f64dw>::value) {
-        if (s.col && !s.general) {
-            const int gx = (s.nx + COL_W - 1) / COL_W, bands = (s.ny + col_h<S>() - 1) / col_h<S>();
+        if (s.col_h > 0 && !s.general) {
+            const int gx = (s.nx + COL_W - 1) / COL_W, bands = (s.ny + s.col_h - 1) / s.col_h;
             const long long warps = (long long)gx * bands;
             const int blocks = (int)((warps + COL_WARPS - 1) / COL_WARPS);
-            k_step_ab_col<S><<<blocks, COL_WARPS * 32, 0, st>>>(a, static_cast<S*>(v.f2), gx, bands);
+            k_step_ab_col<S><<<blocks, COL_WARPS * 32, 0, st>>>(a, static_cast<S*>(v.f2), gx, bands, s.col_h);
             return cudaGetLastError();
         }
     }

@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "lb_ab_col.cuh"
 #include "lb_handle.h"
 
 
@@ -115,16 +116,18 @@ bool auto_vector(const trtrlb_lattice* h) {
 }
 
 // Default two-buffer kernel of a G_CURRENT lattice that is periodic without a
-// mask: the column-walking kernel for FP64, FP16 and BF16 storage at 512^2
-// nodes or more (on 3 x 4096^2 it stepped FP16 in 0.551 ms against 0.696 for
-// the plain kernel, FP64 in 11.66 against 13.75); FP32 keeps the TMA-fed
-// kernel, which measured faster on one 4096^2 lattice (0.231 against
-// 0.239 ms); smaller lattices, whose bands give too few warps, the plain one.
-bool auto_column(const trtrlb_lattice* h) {
+// mask: for FP64, FP16 and BF16 storage the column-walking kernel wherever its
+// bands give enough warps (trt::col_band_rows; on 3 x 4096^2 it stepped FP16
+// in 0.551 ms against 0.696 for the plain kernel, FP64 in 11.66 against
+// 13.75), the plain kernel below that; FP32 keeps the TMA-fed kernel, which
+// measured faster from 2048^2 (one 4096^2 lattice: 0.2297 against 0.2306 ms).
+// Returns the column kernel's rows per band, 0 when it is not the default.
+int auto_column(const trtrlb_lattice* h) {
     const int st = h->p.storage;
-    return h->p.g_mode == TRTRLB_G_CURRENT && !h->s.general &&
-           (st == TRTRLB_F64 || st == TRTRLB_F16_SHIFTED || st == TRTRLB_BF16_SHIFTED) &&
-           (long long)h->p.nx * h->p.ny >= 512ll * 512ll;
+    if (h->p.g_mode != TRTRLB_G_CURRENT || h->s.general ||
+        !(st == TRTRLB_F64 || st == TRTRLB_F16_SHIFTED || st == TRTRLB_BF16_SHIFTED))
+        return 0;
+    return trt::col_band_rows((int)elem_size(st), h->p.nx, h->p.ny, h->sms);
 }
 
 // Staging buffer for host transfers and comparisons: at least `fields` FP64
@@ -277,7 +280,13 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     h->p.magic = (p.tau_s - 0.5) * (tau2 - 0.5);
     h->stream = static_cast<cudaStream_t>(stream);
     const size_t es = elem_size(p.storage), ps = phi_size(p.storage);
-    cudaError_t e;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(err, e, "device query");
+    }
     auto alloc = [&](void** ptr, size_t bytes) {
         e = cudaMalloc(ptr, bytes);
         if (e == cudaSuccess) h->bytes += (int64_t)bytes;
@@ -343,7 +352,7 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
     s.tile_w = h->tile_w;
     h->variant = TRTRLB_KERNEL_AUTO;
     s.vec = auto_vector(h);
-    s.col = auto_column(h);
+    s.col_h = auto_column(h);
     if (p.g_mode == TRTRLB_G_CURRENT && p.storage == TRTRLB_F32 && !s.general) {
         // the TMA-fed two-buffer kernel; without a descriptor the plain one runs
         CUtensorMap* maps = new (std::nothrow) CUtensorMap[2];
@@ -682,7 +691,14 @@ int trtrlb_set_kernel(trtrlb_t h, int32_t variant, int32_t tile_w) {
     }
     h->variant = variant;
     h->s.vec = vec;
-    h->s.col = variant == TRTRLB_KERNEL_COLUMN || (variant == TRTRLB_KERNEL_AUTO && auto_column(h));
+    if (variant == TRTRLB_KERNEL_COLUMN) {
+        // the tallest band that still fills the device, else the shortest
+        const int es = (int)elem_size(h->p.storage);
+        const int band = trt::col_band_rows(es, h->p.nx, h->p.ny, h->sms);
+        h->s.col_h = band > 0 ? band : trt::col_h_max(es) / 4;
+    } else {
+        h->s.col_h = variant == TRTRLB_KERNEL_AUTO ? auto_column(h) : 0;
+    }
     // G_CURRENT: AUTO runs the TMA-fed kernel where it exists, SCALAR the plain
     // one, COLUMN the column-walking one
     h->s.tma_grid = variant == TRTRLB_KERNEL_AUTO || variant == TRTRLB_KERNEL_VECTOR ? h->tma_grid : 0;
@@ -711,7 +727,7 @@ int trtrlb_step_kernel(trtrlb_t h, int32_t* kind) {
         *kind = h->s.vec ? TRTRLB_STEP_AA_VECTOR : TRTRLB_STEP_AA;
     else if (h->p.storage == TRTRLB_F32 && trt::Ops<float>::tma_eligible(h->s))
         *kind = shares_tma_launch(h) ? TRTRLB_STEP_AB_TMA_SHARED : TRTRLB_STEP_AB_TMA;
-    else if (h->s.col && !h->s.general && h->p.storage != TRTRLB_F64_DW)
+    else if (h->s.col_h > 0 && !h->s.general && h->p.storage != TRTRLB_F64_DW)
         *kind = TRTRLB_STEP_AB_COLUMN;
     else
         *kind = TRTRLB_STEP_AB;
@@ -736,6 +752,94 @@ const char* trtrlb_last_error(trtrlb_t h) { return h ? h->err : g_create_err; }
 }  // extern "C"
 
 namespace trt {
+
+// a[k], or null when the array itself is null
+template <typename T>
+static T* at(T* const* a, int k) {
+    return a ? a[k] : nullptr;
+}
+
+// End-to-end solve of several lattices with the copies beside the steps (the
+// body of trtrlb_batch_solve): uploads on `cin`, member k's init, steps and
+// moments on `st`, its downloads on `cout` once its moments are written.
+int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t cin, cudaStream_t cout,
+                  const double* const* rho, const double* const* ux, const double* const* uy, int64_t nsteps,
+                  double* const* rho_out, double* const* ux_out, double* const* uy_out, char* err) {
+    if (count < 0 || (count > 0 && (!m || !ux || !uy)) || nsteps < 0)
+        return fail(err, TRTRLB_EINVAL, "bad member list, input arrays or step count");
+    for (int k = 0; k < count; ++k)
+        if (!m[k] || !ux[k] || !uy[k]) return fail(err, TRTRLB_EINVAL, "every member needs ux and uy");
+    if (count == 0) return TRTRLB_OK;
+    std::vector<cudaEvent_t> ev(2 * (size_t)count + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    // staging for host inputs and outputs (allocated before any copy is queued)
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const void* io[6] = {at(rho, k), ux[k], uy[k], at(rho_out, k), at(ux_out, k), at(uy_out, k)};
+        bool host = false;
+        for (const void* p : io) host = host || (p && !on_device(p));
+        if (host) e = ensure_stage(m[k], 3);
+    }
+    // every member's earlier work (on its own stream) before this call's
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(ev[2 * count], m[k]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[2 * count], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, ev[2 * count], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev[2 * count], 0);
+    }
+    std::vector<const double*> din(3 * (size_t)count, nullptr);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const size_t n = (size_t)m[k]->p.nx * m[k]->p.ny;
+        const double* src[3] = {at(rho, k), ux[k], uy[k]};
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+            if (!src[q] || on_device(src[q])) {
+                din[3 * k + q] = src[q];
+                continue;
+            }
+            e = cudaMemcpyAsync(m[k]->stage + q * n, src[q], n * sizeof(double), cudaMemcpyHostToDevice, cin);
+            din[3 * k + q] = m[k]->stage + q * n;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k], cin);
+    }
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        trtrlb_lattice* h = m[k];
+        const size_t n = (size_t)h->p.nx * h->p.ny;
+        e = cudaStreamWaitEvent(st, ev[k], 0);
+        if (e == cudaSuccess)
+            e = TRT_DISPATCH(h->p.storage, init(h->s, din[3 * k], din[3 * k + 1], din[3 * k + 2], st));
+        if (e != cudaSuccess) break;
+        h->t = 0;
+        for (int64_t q = 0; q < nsteps && e == cudaSuccess; ++q) {
+            e = TRT_DISPATCH(h->p.storage, step(h->s, st));
+            ++h->t;
+        }
+        double* dst[3] = {at(rho_out, k), at(ux_out, k), at(uy_out, k)};
+        double* dev[3] = {nullptr, nullptr, nullptr};
+        for (int q = 0; q < 3; ++q)
+            if (dst[q]) dev[q] = on_device(dst[q]) ? dst[q] : h->stage + q * n;
+        if (e == cudaSuccess && (dev[0] || dev[1] || dev[2]))
+            e = TRT_DISPATCH(h->p.storage, moments(h->s, dev[0], dev[1], dev[2], st));
+        if (e == cudaSuccess) e = cudaEventRecord(ev[count + k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev[count + k], 0);
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+            if (dst[q] && dev[q] != dst[q])
+                e = cudaMemcpyAsync(dst[q], dev[q], n * sizeof(double), cudaMemcpyDeviceToHost, cout);
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(cout), e2 = cudaStreamSynchronize(st),
+                      e3 = cudaStreamSynchronize(cin);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    if (e != cudaSuccess) return cuda_fail(err, e, "solve");
+    for (int k = 0; k < count; ++k)
+        if (const int rc = check_kerr(m[k])) {
+            std::snprintf(err, 256, "%s", m[k]->err);
+            return rc;
+        }
+    return TRTRLB_OK;
+}
+
 int diag_blocks(const State& s) {
     const long long n = (long long)s.nx * s.ny;
     long long b = (n + DIAG_THREADS - 1) / DIAG_THREADS;

@@ -281,6 +281,31 @@ class Batch:
         self._chk(self._lib.trtrlb_batch_step(self._h, int(n)))
         return self
 
+    def solve(self, fields, steps: int, out=None):
+        """End-to-end solve of every member (trtrlb_batch_solve): member k starts
+        from fields[k] = (ux, uy) or (ux, uy, rho), float64 [ny][nx] numpy arrays
+        or torch tensors on the host (page-locked, for the copies to run beside
+        the steps) or the device; it advances `steps` time steps and its
+        (rho, ux, uy) go to out[k] (arrays or tensors, any of them None; out
+        None: new host numpy arrays).  Returns out."""
+        n = len(self.members)
+        if len(fields) != n:
+            raise ValueError("one (ux, uy[, rho]) per member")
+        ins, keep = [[None] * n for _ in range(3)], []
+        for k, (lat, fk) in enumerate(zip(self.members, fields)):
+            sh = lat.shape
+            for q, a in enumerate((fk[2] if len(fk) > 2 else None, fk[0], fk[1])):
+                a = _as_f64(a, sh)
+                keep.append(a)
+                ins[q][k] = _ptr(a, sh)
+        if out is None:
+            out = [tuple(np.empty(lat.shape) for _ in range(3)) for lat in self.members]
+        outs = [[_ptr(o[q], lat.shape) for o, lat in zip(out, self.members)] for q in range(3)]
+        arr = lambda v: (C.c_void_p * max(1, n))(*v)
+        self._chk(self._lib.trtrlb_batch_solve(self._h, arr(ins[0]), arr(ins[1]), arr(ins[2]), int(steps),
+                                               arr(outs[0]), arr(outs[1]), arr(outs[2])))
+        return out
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.trtrlb_batch_destroy(self._h)

@@ -104,3 +104,68 @@ def test_batch_rejects_duplicates(gpu_lib):
     a = gpu_lattice(pr, "f32")
     with pytest.raises(TrtrlbError):
         Batch().set([a, a])
+
+
+@pytest.mark.parametrize("nsteps", [0, 5, 40])
+@pytest.mark.parametrize("g_mode", ["lagged", "current"])
+def test_batch_solve_equals_init_step_moments_alone(gpu_lib, nsteps, g_mode):
+    """trtrlb_batch_solve (uploads and downloads on copy streams beside the
+    members' steps) gives every member the moments of init + step + moments
+    alone, bit for bit, with host (page-locked or not) and device arrays, rho
+    given or not, and some outputs left out."""
+    import torch
+    from paper_2312_10318_gb300.lattice import Batch
+    stream = torch.cuda.Stream()
+    probs = _mixed_problems()
+    lats, alone, fields, out = [], [], [], []
+    for k, (pr, storage) in enumerate(probs):
+        if g_mode == "current" and pr.mask is not None:
+            continue
+        lat = gpu_lattice(pr, storage, g_mode, stream=stream)
+        ref = gpu_lattice(pr, storage, g_mode, stream=stream).init(pr.ux, pr.uy, pr.rho).step(nsteps)
+        alone.append(ref.moments())
+        lats.append(lat)
+        rho = pr.rho
+        if k % 3 == 0:          # page-locked host inputs
+            f = tuple(None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                      for a in (pr.ux, pr.uy, rho))
+        elif k % 3 == 1:        # device inputs
+            f = tuple(None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                      for a in (pr.ux, pr.uy, rho))
+        else:                   # pageable numpy
+            f = (pr.ux, pr.uy, rho)
+        fields.append(f)
+        sh = (pr.ny, pr.nx)
+        if k % 2:
+            out.append(tuple(torch.empty(sh, dtype=torch.float64, device="cuda") for _ in range(3)))
+        else:
+            out.append((None, np.empty(sh), np.empty(sh)))
+    torch.cuda.synchronize()
+    batch = Batch(stream).set(lats)
+    batch.solve(fields, nsteps, out)
+    for lat, (r_rho, r_ux, r_uy), o in zip(lats, alone, out):
+        got = [None if a is None else (a.cpu().numpy() if isinstance(a, torch.Tensor) else a) for a in o]
+        if got[0] is not None:
+            assert np.array_equal(got[0], r_rho)
+        assert np.array_equal(got[1], r_ux) and np.array_equal(got[2], r_uy)
+        assert lat.t == nsteps
+    # the members' states afterwards are those of the lattices stepped alone
+    new = batch.solve([(pr.ux, pr.uy, pr.rho) for pr, _ in probs if g_mode == "lagged" or pr.mask is None], 3)
+    for (rho, ux, uy), lat in zip(new, lats):
+        assert np.array_equal(lat.moments()[1], ux)
+
+
+def test_batch_solve_rejects_bad_arguments(gpu_lib):
+    import torch
+    from paper_2312_10318_gb300._lib import TrtrlbError
+    from paper_2312_10318_gb300.lattice import Batch
+    pr = W.taylor_green(32, 0.04, 100.0)
+    lat = gpu_lattice(pr, "f32")
+    batch = Batch().set([lat])
+    with pytest.raises(ValueError):
+        batch.solve([], 3)
+    with pytest.raises(TrtrlbError):
+        batch.solve([(pr.ux, None)], 3)
+    with pytest.raises(TrtrlbError):
+        batch.solve([(pr.ux, pr.uy)], -1)
+    assert Batch().set([]).solve([], 3) == []

@@ -231,6 +231,29 @@ def test_column_kernel_matches_oracle(gpu_lib, nx, ny, storage):
             check_rounding_bounds("f32", G, R, n, max(d_max, shifted_max(R)))
 
 
+@pytest.mark.parametrize("storage,n", [("f64", 1024), ("f32", 2048)])
+def test_column_kernel_full_bands_match_oracle(gpu_lib, storage, n):
+    """The column kernel on lattices large enough for its tallest bands (16
+    rows in FP64 at 1024^2, 32 in FP32 at 2048^2: every warp walks a full
+    band, and bands meet inside the lattice as well as across the periodic
+    edge) against the oracle's CURRENT mode over 2 steps from random
+    populations: FP64 to 1e-12 per field, FP32 within its rounding bounds."""
+    from helpers import check_rounding_bounds, shifted_max
+    pr = W.Problem("r", n, n, 0.62, 1.3, np.zeros((n, n)), np.zeros((n, n)), g=(2e-5, 1e-5))
+    f0 = W.random_populations(n, n, seed=n + 3, amp=0.2)
+    G = gpu_lattice(pr, storage, "current").set_kernel("column").set_f(f0)
+    assert G.step_kernel() == "ab_column"
+    R = oracle_lattice(pr, "current").set_f(f0)
+    d_max = shifted_max(R)
+    G.step(2)
+    R.step(2)
+    if storage == "f64":
+        errs = field_errors(G, R)
+        assert max(errs.values()) < 1e-12, errs
+    else:
+        check_rounding_bounds("f32", G, R, 2, max(d_max, shifted_max(R)))
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_column_kernel_taylor_green(gpu_lib, storage):
     """The column kernel on the 64^2 Taylor-Green vortex over 1000 steps in the
@@ -261,9 +284,11 @@ def test_column_kernel_only_where_it_applies(gpu_lib):
 @pytest.mark.parametrize("storage", ["f16", "f64"])
 def test_default_current_kernel_by_size(gpu_lib, storage):
     """With G_CURRENT on a periodic lattice without a mask the library steps
-    FP64/FP16/BF16 with the column kernel from 512^2 nodes and with the plain
+    FP64/FP16/BF16 with the column kernel where its bands fill the device
+    (FP16 from 1024^2, FP64 from 512^2 on GB300's 152 SMs) and with the plain
     two-buffer kernel below: the default equals the forced kernel bit for bit."""
-    for n, forced in ((512, "column"), (256, "scalar")):
+    big, small = (1024, 512) if storage == "f16" else (512, 256)
+    for n, forced in ((big, "column"), (small, "scalar")):
         pr = W.double_shear_layer(n, re=1e4)
         a = gpu_lattice(pr, storage, "current").init(pr.ux, pr.uy)
         b = gpu_lattice(pr, storage, "current").set_kernel(forced).init(pr.ux, pr.uy)
@@ -299,16 +324,19 @@ def test_reported_step_kernel(gpu_lib):
     """trtrlb_step_kernel names the kernel the settings select: the AA kernels
     with Phi lagged, and with Phi at the current level the TMA-fed kernel for
     FP32 (shared launches below 2048^2 nodes), the column kernel for FP16 from
-    512^2, the plain one otherwise (walls, small lattices, or forced)."""
-    dsl = {n: W.double_shear_layer(n, re=1e4) for n in (256, 512, 2048)}
+    1024^2 and FP64 from 512^2, the plain one otherwise (walls, small
+    lattices, or forced)."""
+    dsl = {n: W.double_shear_layer(n, re=1e4) for n in (256, 512, 1024, 2048)}
     assert gpu_lattice(dsl[256], "f32", "lagged").step_kernel() == "aa_vector"
     assert gpu_lattice(dsl[256], "f32", "lagged").set_kernel("scalar").step_kernel() == "aa"
     assert gpu_lattice(dsl[256], "f32", "current").step_kernel() == "ab_tma_shared"
     assert gpu_lattice(dsl[2048], "f32", "current").step_kernel() == "ab_tma"
     assert gpu_lattice(dsl[256], "f32", "current").set_kernel("scalar").step_kernel() == "ab"
     assert gpu_lattice(dsl[256], "f32", "current").set_kernel("column").step_kernel() == "ab_column"
-    assert gpu_lattice(dsl[512], "f16", "current").step_kernel() == "ab_column"
-    assert gpu_lattice(dsl[256], "f16", "current").step_kernel() == "ab"
+    assert gpu_lattice(dsl[1024], "f16", "current").step_kernel() == "ab_column"
+    assert gpu_lattice(dsl[512], "f16", "current").step_kernel() == "ab"
+    assert gpu_lattice(dsl[512], "f64", "current").step_kernel() == "ab_column"
+    assert gpu_lattice(dsl[256], "f64", "current").step_kernel() == "ab"
     assert gpu_lattice(dsl[512], "f64dw", "current").step_kernel() == "ab"
     ch = W.poiseuille(16, 0.8, 0.25)
     assert gpu_lattice(ch, "f32", "current").step_kernel() == "ab"
