@@ -658,7 +658,7 @@ def main():
     h2d_bytes = sum(a.numel() * a.element_size() for f in host_in for a in f if a is not None)
     d2h_bytes = sum(a.numel() * a.element_size() for f in host_out for a in f)
     e2e_times = []
-    for rep in range(0 if args.no_e2e else 3):
+    for rep in range(0 if args.no_e2e else 5):
         barrier()
         t0 = time.perf_counter()
         if args.mode == "batch":
@@ -703,6 +703,7 @@ def main():
                          "traffic": None if traffic is None else traffic,
                          "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode)},
             "e2e": {"value": e2e_value, "unit": UNIT,
+                    "solves_ms": [round(t * 1e3, 2) for t in e2e_times],
                     "h2d_bytes_per_step": h2d_bytes / args.e2e_steps,
                     "d2h_bytes_per_step": d2h_bytes / args.e2e_steps,
                     "solve": (f"init from pinned host fields (u; rho where the workload has one) + "
