@@ -17,6 +17,7 @@ events).
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (weak scaling, no collective on the data path); rank 0 prints one JSON line.
+The CPU baseline and the served stream are one-GPU measurements (N = 1 only).
 --impl reference times the FP64 CPU oracle on the same workload on the host
 cores (rank 0 only).
 """
@@ -729,7 +730,9 @@ def main():
                                                  "every step, outside its event pair"}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(problems, g_mode=args.g_mode)
-        if not args.no_serve:
+        if world == 1 and not args.no_serve:
+            # the served stream is a one-GPU measurement: under torchrun the
+            # other GPUs would only wait for it
             line["serving"] = run_serving(args)
         print(json.dumps(line), flush=True)
     batch.close()
