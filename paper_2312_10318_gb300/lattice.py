@@ -218,12 +218,22 @@ class Lattice:
                                          _ptr(phi, (2, self.ny, self.nx))))
         return self
 
-    def diagnostics(self) -> dict:
-        out = np.zeros(8)
-        self._chk(self._lib.trtrlb_diagnostics(self._h, _ptr(out)))
-        keys = ("mass", "momentum_x", "momentum_y", "kinetic_energy", "max_u", "nonfinite",
-                "wall_force_x", "wall_force_y")
-        return dict(zip(keys, out.tolist()))
+    DIAG_KEYS = ("mass", "momentum_x", "momentum_y", "kinetic_energy", "max_u", "nonfinite",
+                 "wall_force_x", "wall_force_y")
+
+    def diagnostics(self, out=None):
+        """FP64 diagnostics of the current state (trtrlb_diagnostics) as a dict
+        keyed by DIAG_KEYS.  With `out` (8 float64 values, a CUDA tensor or a
+        host array) they are written there instead and `out` is returned; into
+        device memory the call does not synchronise."""
+        if out is not None:
+            if (out.size if isinstance(out, np.ndarray) else out.numel()) != 8:
+                raise ValueError("diagnostics need an output of 8 float64 values")
+            self._chk(self._lib.trtrlb_diagnostics(self._h, _ptr(out)))
+            return out
+        o = np.zeros(8)
+        self._chk(self._lib.trtrlb_diagnostics(self._h, _ptr(o)))
+        return dict(zip(self.DIAG_KEYS, o.tolist()))
 
     COMPARE_KEYS = ("l2_u", "max_du", "l2_vorticity", "rms_du", "sum_du2", "sum_uref2", "sum_dw2",
                     "sum_wref2", "nodes", "nonfinite")

@@ -195,6 +195,22 @@ def velocity_scale(spec) -> float:
     return float(m.get("u0", m.get("u_c", 0.04)))
 
 
+def diagnose(lats, stream) -> list:
+    """Diagnostics (dicts keyed by Lattice.DIAG_KEYS) of several lattices with
+    one synchronisation: every lattice's reduction into one device array, then
+    one copy to the host.  The lattices' work must be ordered on `stream`."""
+    import torch
+    from .lattice import Lattice
+    if not lats:
+        return []
+    with torch.cuda.stream(stream):
+        buf = torch.empty((len(lats), 8), dtype=torch.float64, device="cuda")
+        for k, lat in enumerate(lats):
+            lat.diagnostics(out=buf[k])
+        host = buf.cpu().numpy()
+    return [dict(zip(Lattice.DIAG_KEYS, row.tolist())) for row in host]
+
+
 class PrecisionGuard:
     """Admission-time check of a reduced-precision solve against FP64.
 
@@ -344,9 +360,11 @@ class Server:
         import torch
         from .lattice import Batch
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        # admission (lattice set-up and the guard's probes) runs on its own
-        # stream, beside the chunk in flight on self.stream
+        # admission (lattice set-up and the guard's probes) and retirement (the
+        # finished solves' diagnostics) run on streams of their own, beside
+        # the chunk in flight on self.stream
         self.admit_stream = torch.cuda.Stream()
+        self.retire_stream = torch.cuda.Stream()
         self.batch = Batch(self.stream)
         self.defer_bytes = float(defer_bytes)
         self._deferred = []            # lattices to free after the chunk in flight
@@ -439,13 +457,15 @@ class Server:
     def run(self, requests: list, realtime: bool = True) -> list:
         """Serves the stream; with realtime=False every request is available at once.
 
-        One scheduling point per chunk.  The chunk's steps are launched for the
-        active lattices; while the GPU runs them the host admits waiting
-        requests (their lattices are made, initialised and checked by the
-        precision guard on the admission stream, so that work shares the GPU
-        with the chunk), then waits for the chunk, retires the solves that are
-        done, frees what was released, and adds the admitted lattices to the
-        next chunk."""
+        One scheduling point per chunk.  While the GPU runs a chunk the host
+        admits waiting requests (their lattices are made, initialised and
+        checked by the precision guard on the admission stream, so that work
+        shares the GPU with the chunk).  At the chunk's end it frees what was
+        released, launches the next chunk for the solves that go on and the
+        admitted ones, and only then retires the solves that are done (their
+        diagnostics on the retirement stream, beside the new chunk).  Every
+        check_every chunks the diagnostics of all active solves are taken
+        before the next launch, to retire unstable ones."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting, active, results = [], [], []
@@ -474,6 +494,7 @@ class Server:
                     break
                 waiting.pop(0)
                 admitted.append(a)
+            finishing = []         # (solve, its diagnostics or None)
             if in_flight:
                 self.stream.synchronize()
                 n, in_flight = in_flight, 0
@@ -481,22 +502,17 @@ class Server:
                 self.node_updates += n * sum(a.req.n * a.req.n for a in active)
                 for a in active:
                     a.remaining -= n
-                now = clock()
                 check = self.check_every > 0 and chunks % self.check_every == 0
+                diags = diagnose([a.lat for a in active], self.stream) if check else [None] * len(active)
+                now = clock()
                 keep = []
-                for a in active:
-                    if a.req.rid in self._cancelled and a.remaining > 0:
-                        results.append(self._retire(a, now, "cancelled", a.lat.diagnostics()))
-                        continue
-                    if a.remaining == 0 or check:
-                        d = a.lat.diagnostics()
-                        if self._unstable(d):
-                            results.append(self._retire(a, now, "unstable", d))
-                            continue
-                        if a.remaining == 0:
-                            results.append(self._retire(a, now, "ok", d))
-                            continue
-                    keep.append(a)
+                for a, d in zip(active, diags):
+                    if d is not None and self._unstable(d):
+                        results.append(self._retire(a, now, "unstable", d))
+                    elif a.remaining == 0 or a.req.rid in self._cancelled:
+                        finishing.append((a, d))
+                    else:
+                        keep.append(a)
                 active = keep
             if admitted:
                 # the batch's stream takes over the admitted lattices after the
@@ -508,20 +524,35 @@ class Server:
                     a.lat.set_stream(self.stream)
                 active.extend(admitted)
             self._flush()          # nothing in flight: freeing waits for no kernel
-            if not active:
-                if members:
-                    self.batch.set([])
-                    members = None
-                if pending and not waiting:
-                    time.sleep(max(0.0, min(0.05, pending[0].arrival - clock())))
-                continue
-            lats = [a.lat for a in active]
-            if members is None or len(members) != len(lats) or any(x is not y for x, y in zip(members, lats)):
-                self.batch.set(lats)
-                members = lats
-            n = min(self.chunk, min(a.remaining for a in active))
-            self.batch.step(n)
-            in_flight = n
+            if active:
+                lats = [a.lat for a in active]
+                if members is None or len(members) != len(lats) or any(x is not y for x, y in zip(members, lats)):
+                    self.batch.set(lats)
+                    members = lats
+                n = min(self.chunk, min(a.remaining for a in active))
+                self.batch.step(n)
+                in_flight = n
+            elif members:
+                self.batch.set([])
+                members = None
+            if finishing:
+                # the finished solves left the batch; their last work is done,
+                # so their diagnostics run beside the new chunk
+                need = [a for a, d in finishing if d is None]
+                for a in need:
+                    a.lat.set_stream(self.retire_stream)
+                got = iter(diagnose([a.lat for a in need], self.retire_stream))
+                now = clock()
+                for a, d in finishing:
+                    d = d if d is not None else next(got)
+                    if a.req.rid in self._cancelled and a.remaining > 0:
+                        status = "cancelled"
+                    else:
+                        status = "unstable" if self._unstable(d) else "ok"
+                    results.append(self._retire(a, now, status, d))
+            if not active and not in_flight and pending and not waiting:
+                time.sleep(max(0.0, min(0.05, pending[0].arrival - clock())))
+        self._flush()
         self.makespan = clock()
         return sorted(results, key=lambda r: r.rid)
 
