@@ -6,6 +6,7 @@
 #include "lb_ops.cuh"
 
 #include <type_traits>
+#include <utility>
 
 namespace trt {
 
@@ -21,6 +22,77 @@ __device__ __forceinline__ df64 aux_widen(const df64& v) { return v; }
 template <typename A>
 __device__ __forceinline__ A aux_sel(int c, const A& x) {
     return c > 0 ? x : (c < 0 ? -x : A(0));
+}
+
+// A double-word constant, split at compile time (no FP64 instruction runs).
+__host__ __device__ constexpr df64 dw_const(double x) {
+    return df64((float)x, (float)(x - (double)(float)x));
+}
+
+// Direction I of the initial state in double-word arithmetic (k_init), its
+// lattice constants fixed at compile time.
+template <int I, typename S>
+__device__ __forceinline__ void init_dir(S* F, long long plane, long long own, const df64& r, const df64& u,
+                                         const df64& v, const df64& uu, const df64& vv, const df64& uv,
+                                         const df64& uuv, const df64& uvv, const df64& Fx, const df64& Fy,
+                                         const df64& r0) {
+    using A = df64;
+    using C = typename Fmt<S>::C;
+    constexpr int cx = ex(I), cy = ey(I);
+    constexpr A KX = dw_const(cx * cx - 1.0 / 3.0), KY = dw_const(cy * cy - 1.0 / 3.0);
+    constexpr A W = dw_const(wgt(I)), W15 = dw_const(1.5 * wgt(I));
+    constexpr A ONE = dw_const(1.0), THREE = dw_const(3.0), K45 = dw_const(4.5), K135 = dw_const(13.5);
+    const A eu = aux_sel(cx, u) + aux_sel(cy, v);
+    A huu = KX * uu + KY * vv;
+    if constexpr (cx * cy != 0) huu = huu + aux_sel(cx * cy, uv + uv);
+    const A h3 = aux_sel(cy, KX * uuv) + aux_sel(cx, KY * uvv);
+    const A feq = W * r * (ONE + THREE * eu + K45 * huu + K135 * h3);
+    const A eF = aux_sel(cx, Fx) + aux_sel(cy, Fy);
+    C out;
+    aux_round(feq - W15 * eF - W * r0, out);
+    F[(long long)I * plane + own] = Fmt<S>::st(out);
+}
+
+template <typename S, int... I>
+__device__ __forceinline__ void init_dirs(std::integer_sequence<int, I...>, S* F, long long plane, long long own,
+                                          const df64& r, const df64& u, const df64& v, const df64& uu,
+                                          const df64& vv, const df64& uv, const df64& uuv, const df64& uvv,
+                                          const df64& Fx, const df64& Fy, const df64& r0) {
+    (init_dir<I, S>(F, plane, own, r, u, v, uu, vv, uv, uuv, uvv, Fx, Fy, r0), ...);
+}
+
+// Direction I of the initial state for FP32 and 16-bit storage (k_init):
+// d_i = w_i [drho + 3 e_i.(rho u) + T], T in FP32.
+template <int I, typename S>
+__device__ __forceinline__ void init_dir_mixed(S* F, long long plane, long long own, const df64& dr,
+                                               const df64& ru, const df64& rv, float rf, float uf, float vf,
+                                               float gx, float gy) {
+    using C = typename Fmt<S>::C;
+    constexpr int cx = ex(I), cy = ey(I);
+    constexpr float kx = (float)(cx * cx) - 1.0f / 3.0f, ky = (float)(cy * cy) - 1.0f / 3.0f;
+    constexpr df64 W = dw_const(wgt(I));
+    const df64 eru = aux_sel(cx, ru) + aux_sel(cy, rv);            // e_i.(rho u)
+    df64 s3;                                                        // 3 e_i.(rho u), exact scaling by 3
+    two_prod(eru.hi, 3.0f, s3.hi, s3.lo);
+    s3.lo = fmaf(eru.lo, 3.0f, s3.lo);
+    fast_two_sum(s3.hi, s3.lo, s3.hi, s3.lo);
+    const float huu = kx * uf * uf + ky * vf * vf + (float)(2 * cx * cy) * uf * vf;
+    const float h3 = kx * (float)cy * uf * uf * vf + ky * (float)cx * uf * vf * vf;
+    const float t = rf * (4.5f * huu + 13.5f * h3 - 1.5f * ((float)cx * gx + (float)cy * gy));
+    df64 sum = dr + s3;
+    float sh, sl;
+    two_sum(sum.hi, t, sh, sl);
+    fast_two_sum(sh, __fadd_rn(sl, sum.lo), sum.hi, sum.lo);
+    C out;
+    aux_round(W * sum, out);
+    F[(long long)I * plane + own] = Fmt<S>::st(out);
+}
+
+template <typename S, int... I>
+__device__ __forceinline__ void init_dirs_mixed(std::integer_sequence<int, I...>, S* F, long long plane,
+                                                long long own, const df64& dr, const df64& ru, const df64& rv,
+                                                float rf, float uf, float vf, float gx, float gy) {
+    (init_dir_mixed<I, S>(F, plane, own, dr, ru, rv, rf, uf, vf, gx, gy), ...);
 }
 
 // Phi of non-fluid nodes (reading of the paper's silence on walls): 0 at
@@ -94,27 +166,36 @@ __global__ void k_init(Args<typename Fmt<S>::C> a, const double* __restrict__ rh
         const C px = (C)(r * u * u * u), py = (C)(r * v * v * v);
         a.phi_out[own] = px; a.phi_out[a.plane + own] = py;
         phi_b[own] = px; phi_b[a.plane + own] = py;
+    } else if constexpr (!std::is_same<S, f64dw>::value) {
+        // FP32 and the 16-bit formats, whose stores round to 2^-24 or coarser:
+        // d_i / w_i = drho + 3 e_i.(rho u) + rho (4.5 H:uu + 13.5 H3:uuu
+        // - 1.5 e_i.g), the first two terms (up to ~0.3) in double-word
+        // arithmetic, the rest (|.| <~ 0.1 rho) in FP32, whose error there,
+        // 2^-24 of it, stays below one rounding of the stored value; the inputs
+        // split without FP64 instructions
+        using A = df64;
+        const A r = df64_split(rho ? rho[k] : rho0);
+        const A u = df64_split(ux[k]), v = df64_split(uy[k]);
+        const A dr = rho ? r - df64_split(rho0) : A(0.f, 0.f);
+        const A ru = r * u, rv = r * v;
+        const float rf = r.hi, uf = u.hi, vf = v.hi;
+        const float fgx = a.gx, fgy = a.gy;   // the FP32 arguments: no conversion per node
+        init_dirs_mixed<S>(std::make_integer_sequence<int, 9>{}, F, a.plane, own, dr, ru, rv, rf, uf, vf, fgx, fgy);
+        C px, py;
+        aux_round(r * (u * u) * u, px);
+        aux_round(r * (v * v) * v, py);
+        a.phi_out[own] = px; a.phi_out[a.plane + own] = py;
+        phi_b[own] = px; phi_b[a.plane + own] = py;
     } else {
         // the same equilibrium, with the velocity products shared by the directions
         using A = df64;
-        const A r = A(rho ? rho[k] : rho0);
-        const A u = A(ux[k]), v = A(uy[k]);
+        auto in = [](double x) { return A(x); };
+        const A r = in(rho ? rho[k] : rho0);
+        const A u = in(ux[k]), v = in(uy[k]);
         const A uu = u * u, vv = v * v, uv = u * v, uuv = uu * v, uvv = u * vv;
-        const A Fx = r * A(gx), Fy = r * A(gy), r0 = A(rho0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int cx = ex(i), cy = ey(i);
-            const double kx = cx * cx - 1.0 / 3.0, ky = cy * cy - 1.0 / 3.0, w = wgt(i);
-            const A eu = aux_sel(cx, u) + aux_sel(cy, v);
-            A huu = A(kx) * uu + A(ky) * vv;
-            if (cx * cy != 0) huu = huu + aux_sel(cx * cy, uv + uv);
-            const A h3 = aux_sel(cy, A(kx) * uuv) + aux_sel(cx, A(ky) * uvv);
-            const A feq = A(w) * r * (A(1) + A(3.0) * eu + A(4.5) * huu + A(13.5) * h3);
-            const A eF = aux_sel(cx, Fx) + aux_sel(cy, Fy);
-            C out;
-            aux_round(feq - A(1.5 * w) * eF - A(w) * r0, out);
-            F[(long long)i * a.plane + own] = Fmt<S>::st(out);
-        }
+        const A Fx = r * in(gx), Fy = r * in(gy), r0 = in(rho0);
+        init_dirs<S>(std::make_integer_sequence<int, 9>{}, F, a.plane, own, r, u, v, uu, vv, uv, uuv, uvv, Fx,
+                     Fy, r0);
         C px, py;
         aux_round(r * uu * u, px);
         aux_round(r * vv * v, py);
@@ -161,9 +242,9 @@ __global__ void k_moments(Args<typename Fmt<S>::C> a, double* rho, double* ux, d
         if (c == PRESSURE) zh_fill<df64>(d, aux_widen(a.zh_dr));
         df64 r, u, v;
         moments_of<df64>(d, aux_widen(a.gx), aux_widen(a.gy), aux_widen(a.rho0), r, u, v);
-        if (rho) rho[k] = (double)r;
-        if (ux) ux[k] = (double)u;
-        if (uy) uy[k] = (double)v;
+        if (rho) rho[k] = dw_to_double(r);
+        if (ux) ux[k] = dw_to_double(u);
+        if (uy) uy[k] = dw_to_double(v);
     }
 }
 

@@ -81,6 +81,49 @@ __device__ __forceinline__ df64 operator/(const df64& x, const df64& y) { return
 __device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { return x = x + y; }
 __device__ __forceinline__ df64& operator-=(df64& x, const df64& y) { return x = x - y; }
 
+// A double as a double-word pair without FP64 instructions, which GB300 runs
+// at a small fraction of the FP32 rate: hi takes the top 24 significant bits
+// of x and lo the next 23 (truncated, |x - hi - lo| < 2^-46 |x|), both by bit
+// manipulation and one exact FP32 subtraction (2^e (1 + m 2^-23) - 2^e).
+// Magnitudes outside [2^-103, 2^128) other than zero, where lo would leave
+// the normal FP32 range, take the FP64 conversion of df64(double).
+// The FP64 conversion as a call of its own, so that the compiler does not
+// evaluate it alongside the bit manipulation and select (this is the rare
+// path).
+static __device__ __noinline__ df64 df64_of_double(double x) { return df64(x); }
+
+__device__ __forceinline__ df64 df64_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if ((b << 1) == 0ull) return df64(0.f, 0.f);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int dexp = (int)((hw >> 20) & 0x7ffu);
+    if (dexp < 1023 - 103 || dexp > 1023 + 127) return df64_of_double(x);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned e = (unsigned)(dexp - 1023 + 127);              // biased FP32 exponent of x
+    const unsigned mhi = ((hw & 0xfffffu) << 3) | (lw >> 29);      // mantissa bits 51..29
+    const unsigned mlo = (lw >> 6) & 0x7fffffu;                    // mantissa bits 28..6
+    const float hi = __uint_as_float(sign | (e << 23) | mhi);
+    const float unit = __uint_as_float(sign | ((e - 23u) << 23));  // the last place of hi
+    const float lo = __fsub_rn(__uint_as_float(sign | ((e - 23u) << 23) | mlo), unit);
+    return df64(hi, lo);
+}
+
+// A float widened to double from its bits: exact, like the conversion, but
+// without an FP64 instruction.  Subnormal, infinite and NaN inputs take the
+// conversion (out of line, so that it is not evaluated alongside).
+static __device__ __noinline__ double f64_of_float_slow(float x) { return (double)x; }
+__device__ __forceinline__ double f64_of_float(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u && (b & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);   // +-0
+    if (e == 0u || e == 0xffu) return f64_of_float_slow(x);
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+// hi + lo in double: the same sum as (double)hi + (double)lo, one FP64 add.
+__device__ __forceinline__ double dw_to_double(df64 v) { return f64_of_float(v.hi) + f64_of_float(v.lo); }
+
 // storage tag: a double-word pair in memory (hi at the lower address)
 struct __align__(8) f64dw {
     float hi, lo;

@@ -108,3 +108,25 @@ def test_fp32_large_relaxation_time(gpu_lib):
     err = max(O.l2(u["f32"][q], u["f64"][q]) for q in range(2))
     print(f"tau1={pr.tau_s:.0f}: FP32 vs FP64 velocity after 10000 steps: {err:.3e}")
     assert np.isfinite(err) and err < 1e-3
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_init_splits_inputs_of_every_magnitude(gpu_lib, storage):
+    """The initial state of the reduced formats takes its FP64 inputs apart
+    into FP32 pairs by bit manipulation (values from 2^-103 up, and zeros) or,
+    outside that range, by the FP64 conversion: fields mixing zeros, values of
+    both signs from 1e-40 to 0.05 and a non-uniform density give every field
+    (rho, u, each f_i) within one store rounding of the oracle's
+    initialisation."""
+    n = 48
+    r = np.random.default_rng(11)
+    mag = 10.0 ** r.uniform(-40, np.log10(0.05), size=(n, n))
+    ux = mag * r.choice([-1.0, 1.0], size=(n, n))
+    uy = np.roll(ux, 7, axis=1) * 0.5
+    ux[::5, ::3] = 0.0
+    uy[1::4, ::2] = -0.0
+    rho = 1.0 + 0.01 * r.standard_normal((n, n))
+    pr = W.Problem("mix", n, n, 0.8, 1.1, ux, uy, rho)
+    G = gpu_lattice(pr, storage).init(ux, uy, rho)
+    R = oracle_lattice(pr).init(ux, uy, rho)
+    check_rounding_bounds(storage, G, R, 0, shifted_max(R))
