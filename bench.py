@@ -79,6 +79,21 @@ def workload(name: str, size=None, storage=None, g_mode: str = "lagged"):
             p = _rect(p, nx, ny)
         st = storage or "f32"
         return [p], st, f"double shear layer, 1 lattice {nx}x{ny} periodic, Re 1e5, {st.upper()} storage, G {g_mode}"
+    if name == "creeping4096x2048":
+        # the creeping-flow configuration: a 64^2 solid square at x = 1024, moving-wall
+        # inlet column, zero-gradient outlet ghosts, y periodic (mask: 1 B per node)
+        nx, ny = (4096, 2048) if size is None else size
+        p = W.creeping_flow(nx, ny, 64, center_x=nx // 4, re=1.0, ma=0.1)
+        st = storage or "f32"
+        return [p], st, (f"creeping flow past a 64x64 square, {nx}x{ny}, inlet / zero-gradient outlet, "
+                         f"y periodic, Re 1 (Ma 0.1), {st.upper()} storage, G {g_mode}")
+    if name == "channel4096":
+        # force-driven channel with half-way walls in y (the walled kernel, no mask)
+        nx, ny = (4096, 4096) if size is None else size
+        p = W.poiseuille(ny, 0.8, 3.0 / 16.0, nx=nx, u_c=0.01)
+        st = storage or "f32"
+        return [p], st, (f"force-driven channel {nx}x{ny}, half-way walls in y, tau_s 0.8, magic 3/16, "
+                         f"{st.upper()} storage, G {g_mode}")
     if name == "tg64":
         probs = [W.taylor_green(64, 0.04, 100.0, magic=0.25)]
         st = storage or "f64"
@@ -95,14 +110,14 @@ def _rect(p, nx, ny):
     return p
 
 
-def bytes_per_node(storage: str, g_mode: str = "lagged") -> int:
+def bytes_per_node(storage: str, g_mode: str = "lagged", mask: bool = False) -> int:
     """Algorithmic bytes of one node update: 9 populations read and written, plus
     (lagged G) two Phi values read and two written; the current-Phi kernel
-    computes Phi on chip and moves populations only."""
+    computes Phi on chip and moves populations only; a mask adds its byte."""
     b = 2 * 9 * STORAGE_BYTES[storage]
     if g_mode == "lagged":
         b += 4 * PHI_BYTES[storage]
-    return b
+    return b + (1 if mask else 0)
 
 
 # FP64 storage runs its collision on GB300's FP64 pipe, which bounds it long
@@ -640,7 +655,8 @@ def main():
     per_step_launches = step_launches(args.mode, kinds)
     launches = args.steps * per_step_launches
     launch_s = local_ms / 1e3 / launches
-    per_launch_bytes = bytes_per_node(storage, args.g_mode) * nodes / per_step_launches
+    masked = any(p.mask is not None for p in problems)
+    per_launch_bytes = bytes_per_node(storage, args.g_mode, masked) * nodes / per_step_launches
     achieved = per_launch_bytes / launch_s / 1e9
     peak, peak_kind = hbm_peak()
     steady_gbs = per_launch_bytes * per_step_launches * steady_n / (steady_ms / 1e3) / 1e9
@@ -702,7 +718,7 @@ def main():
                         {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic is None else traffic,
-                         "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode)},
+                         "algorithmic_bytes_per_node": bytes_per_node(storage, args.g_mode, masked)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "solves_ms": [round(t * 1e3, 2) for t in e2e_times],
                     "h2d_bytes_per_step": h2d_bytes / args.e2e_steps,

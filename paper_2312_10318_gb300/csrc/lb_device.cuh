@@ -74,6 +74,8 @@ template <typename C> struct Args {
     const C* phi_in;      // [2][ny][pitch]: Phi of the previous level
     C* phi_out;           // [2][ny][pitch]: Phi of this level
     const uint8_t* mask;  // [ny][pitch] or nullptr
+    const uint8_t* seg;   // [ny][segs]: 1 where a 32-node row segment and its neighbours are plain fluid
+    int segs;
     int nx, ny, pitch;
     long long plane;      // ny * pitch
     int px, py;           // periodic flags
@@ -403,12 +405,21 @@ __device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, 
 // Resident 256-thread CTAs per SM the scalar step kernels ask the compiler to
 // allow: the FP32 periodic step with lagged G fits 40 registers without
 // spilling (6 CTAs, 75 % occupancy for the odd step instead of 5), the
-// periodic double-word step 64 (4 CTAs; the odd step took 79 and 3); the
-// other variants keep the compiler's choice.
+// periodic double-word step 64 (4 CTAs; the odd step took 79 and 3).  The
+// general steps (walls, masks, open edges) run the periodic code on interior
+// row segments, so their own code may spill a little: FP32 and 16-bit 6 CTAs
+// (40 registers; 12-80 bytes of spills in the boundary code), double-word 3
+// (72-80 registers, no spills).  Measured on 4096 x 2048 creeping flow and a
+// 4096^2 channel (ms per step, compiler's choice / these): FP32 0.1635 /
+// 0.1442 and 0.2984 / 0.2630, FP16 0.1316 / 0.1138 and 0.2367 / 0.2017,
+// F64_DW 0.3826 / 0.3550 and 0.8070 / 0.7558.  The other variants keep the
+// compiler's choice.
 template <typename S, bool GENERAL, int GMODE>
 __host__ __device__ constexpr int step_min_blocks() {
     return (sizeof(S) == 4 && !GENERAL && GMODE == G_LAGGED) ? 6
+           : (sizeof(S) <= 4 && GENERAL)                          ? 6
            : (std::is_same<S, f64dw>::value && !GENERAL)          ? 4
+           : (std::is_same<S, f64dw>::value && GENERAL)           ? 3
                                                                    : 1;
 }
 
@@ -476,6 +487,13 @@ template <typename S, bool ODD, bool GENERAL, int GMODE>
 __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int x, int y) {
     using C = typename Fmt<S>::C;
     if constexpr (!GENERAL) {
+        node_step_periodic<S, ODD, GMODE>(a, x, y);
+        return;
+    }
+    // a row segment whose nodes and their neighbours are all plain fluid (no
+    // wall, mask class or open edge on any link; a warp is one segment, so
+    // the branch is uniform): the periodic step's code, same arithmetic
+    if (a.seg && a.seg[y * a.segs + (x >> 5)]) {
         node_step_periodic<S, ODD, GMODE>(a, x, y);
         return;
     }

@@ -15,6 +15,7 @@ struct trtrlb_lattice {
     void* f2;            // second population buffer (G_CURRENT only)
     void* phi;           // both Phi buffers in one allocation
     uint8_t* mask;
+    uint8_t* seg;        // interior row segments of a general lattice (State::seg), or null
     int* ghosts;
     double* stage;       // FP64 staging for host transfers and comparisons
     int stage_fields;    // its size in fields of nx * ny doubles (3, 4 or 11)

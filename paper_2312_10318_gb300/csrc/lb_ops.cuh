@@ -37,6 +37,9 @@ struct State {
     void* phi[2];         // Phi buffers, C[2][ny][pitch]
     int cur;              // phi[cur] holds the previous level
     const uint8_t* mask;  // device [ny][pitch] or nullptr
+    const uint8_t* seg;   // general lattices: device [ny][segs], 1 where the 32-node row
+                          // segment and all its neighbours are plain fluid (or nullptr)
+    int segs;             // segments per row, (nx + 31) / 32
     const int* ghosts;    // device list of outlet ghost offsets
     int nghost;
     int nx, ny, pitch;

@@ -19,6 +19,8 @@ static Args<C> make_args(const State& s, bool swap_phi = false) {
     a.phi_in = static_cast<const C*>(s.phi[in]);
     a.phi_out = static_cast<C*>(s.phi[1 - in]);
     a.mask = s.mask;
+    a.seg = s.seg;
+    a.segs = s.segs;
     a.nx = s.nx; a.ny = s.ny; a.pitch = s.pitch; a.plane = s.plane;
     a.px = s.px; a.py = s.py;
     const double k1 = 1.0 - 1.0 / s.tau1, k2 = 1.0 - 1.0 / s.tau2;

@@ -80,6 +80,7 @@ void release(trtrlb_lattice* h) {
     if (h->phi) cudaFree(h->phi);
     if (h->mask) cudaFree(h->mask);
     if (h->ghosts) cudaFree(h->ghosts);
+    if (h->seg) cudaFree(h->seg);
     if (h->stage) cudaFree(h->stage);
     if (h->part) cudaFree(h->part);
     if (h->dout) cudaFree(h->dout);
@@ -128,6 +129,35 @@ int auto_column(const trtrlb_lattice* h) {
         !(st == TRTRLB_F64 || st == TRTRLB_F16_SHIFTED || st == TRTRLB_BF16_SHIFTED))
         return 0;
     return trt::col_band_rows((int)elem_size(st), h->p.nx, h->p.ny, h->sms);
+}
+
+// Row segments of 32 nodes (x = 32 s .. 32 s + 31 of row y) whose nodes are
+// plain fluid nodes, and so is each of their eight neighbours, inside the
+// domain or across a periodic edge: walls, mask classes and open edges touch
+// none of their links, so the general step runs the periodic step's code
+// there.  A 3 x 3 erosion of the fluid set, then an AND per segment.
+std::vector<uint8_t> interior_segments(const uint8_t* mask, int nx, int ny, bool px, bool py) {
+    const int segs = (nx + 31) / 32;
+    std::vector<uint8_t> fl((size_t)nx * ny), hx((size_t)nx * ny), seg((size_t)ny * segs, 0);
+    for (size_t k = 0; k < fl.size(); ++k) fl[k] = !mask || mask[k] == TRTRLB_FLUID;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t r = (size_t)y * nx;
+            const bool l = x > 0 ? fl[r + x - 1] : (px && fl[r + nx - 1]);
+            const bool rr = x < nx - 1 ? fl[r + x + 1] : (px && fl[r]);
+            hx[r + x] = fl[r + x] && l && rr;
+        }
+    for (int y = 0; y < ny; ++y) {
+        const int ym = y > 0 ? y - 1 : (py ? ny - 1 : -1), yp = y < ny - 1 ? y + 1 : (py ? 0 : -1);
+        for (int sgi = 0; sgi < segs; ++sgi) {
+            bool ok = ym >= 0 && yp >= 0;
+            const int x1 = sgi * 32 + 32 < nx ? sgi * 32 + 32 : nx;
+            for (int x = sgi * 32; ok && x < x1; ++x)
+                ok = hx[(size_t)y * nx + x] && hx[(size_t)ym * nx + x] && hx[(size_t)yp * nx + x];
+            seg[(size_t)y * segs + sgi] = ok ? 1 : 0;
+        }
+    }
+    return seg;
 }
 
 // Staging buffer for host transfers and comparisons: at least `fields` FP64
@@ -337,6 +367,21 @@ int trtrlb_create(const trtrlb_params* pp, const uint8_t* mask, void* stream, tr
             release(h);
             return rc;
         }
+    }
+    if (s.general) {
+        const std::vector<uint8_t> seg = interior_segments(mask, p.nx, p.ny, p.periodic_x, p.periodic_y);
+        e = cudaMalloc((void**)&h->seg, seg.size());
+        if (e == cudaSuccess) {
+            h->bytes += (int64_t)seg.size();
+            e = cudaMemcpy(h->seg, seg.data(), seg.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            const int rc = cuda_fail(err, e, "segment map");
+            release(h);
+            return rc;
+        }
+        s.seg = h->seg;
+        s.segs = (p.nx + 31) / 32;
     }
     e = cudaMemsetAsync(h->f, 0, es * 9 * plane, h->stream);
     if (e == cudaSuccess && h->f2) e = cudaMemsetAsync(h->f2, 0, es * 9 * plane, h->stream);
