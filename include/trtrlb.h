@@ -395,8 +395,9 @@ int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps);
  * The members advance one after another, each with its own launches (as
  * trtrlb_step), so that the upload of the next member and the download of
  * the previous one run on two copy streams of the batch while a member
- * steps; the results equal trtrlb_init, trtrlb_step and trtrlb_moments of
- * each member alone.  Ordered after the work already queued on the members'
+ * steps, and the next member's initial state and the previous one's moments
+ * on a fourth stream; the results equal trtrlb_init, trtrlb_step and
+ * trtrlb_moments of each member alone.  Ordered after the work already queued on the members'
  * streams and on the batch's stream; returns when the outputs are written.
  * EINVAL for a bad argument, ECUDA for a CUDA error, ETIMEOUT as
  * trtrlb_moments. */

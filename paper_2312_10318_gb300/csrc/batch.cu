@@ -25,8 +25,9 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity and P
 
 struct trtrlb_batch {
     cudaStream_t stream = nullptr;
-    cudaStream_t copy_in = nullptr;    // uploads and downloads of trtrlb_batch_solve
-    cudaStream_t copy_out = nullptr;   // (created on its first call)
+    cudaStream_t copy_in = nullptr;    // uploads, downloads, and initial states and
+    cudaStream_t copy_out = nullptr;   // moments, of trtrlb_batch_solve (created on
+    cudaStream_t aux = nullptr;        // its first call)
     std::vector<trtrlb_t> lats;
     cudaGraphExec_t graph = nullptr;
     std::vector<int> graph_sig;   // (parity, cur) of every member when captured
@@ -171,6 +172,7 @@ int trtrlb_batch_destroy(trtrlb_batch_t b) {
     drop_graph(b);
     if (b->copy_in) cudaStreamDestroy(b->copy_in);
     if (b->copy_out) cudaStreamDestroy(b->copy_out);
+    if (b->aux) cudaStreamDestroy(b->aux);
     delete b;
     return TRTRLB_OK;
 }
@@ -198,9 +200,16 @@ int trtrlb_batch_solve(trtrlb_batch_t b, const double* const* rho, const double*
     cudaError_t e = cudaSuccess;
     if (!b->copy_in) e = cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking);
     if (e == cudaSuccess && !b->copy_out) e = cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(b, e, "copy streams");
-    return trt::solve_members(b->lats.data(), (int)b->lats.size(), b->stream, b->copy_in, b->copy_out, rho, ux,
-                              uy, nsteps, rho_out, ux_out, uy_out, b->err);
+    if (e == cudaSuccess && !b->aux) {
+        // the highest priority: its short, compute-bound kernels are scheduled
+        // between the steps' blocks instead of after them
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->aux, cudaStreamNonBlocking, hi);
+    }
+    if (e != cudaSuccess) return cuda_fail(b, e, "solve streams");
+    return trt::solve_members(b->lats.data(), (int)b->lats.size(), b->stream, b->aux, b->copy_in, b->copy_out,
+                              rho, ux, uy, nsteps, rho_out, ux_out, uy_out, b->err);
 }
 
 int trtrlb_batch_step(trtrlb_batch_t b, int64_t nsteps) {

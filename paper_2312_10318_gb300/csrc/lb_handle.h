@@ -44,8 +44,10 @@ inline bool shares_tma_launch(const trtrlb_lattice* h) {
 
 namespace trt {
 // Body of trtrlb_batch_solve over the members m[0 .. count): see trtrlb.h.
-// st runs the members' kernels; cin and cout their uploads and downloads.
-int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t cin, cudaStream_t cout,
-                  const double* const* rho, const double* const* ux, const double* const* uy, int64_t nsteps,
-                  double* const* rho_out, double* const* ux_out, double* const* uy_out, char* err);
+// st runs the members' steps, aux their initial states and moments; cin and
+// cout their uploads and downloads.
+int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t aux, cudaStream_t cin,
+                  cudaStream_t cout, const double* const* rho, const double* const* ux, const double* const* uy,
+                  int64_t nsteps, double* const* rho_out, double* const* ux_out, double* const* uy_out,
+                  char* err);
 }  // namespace trt

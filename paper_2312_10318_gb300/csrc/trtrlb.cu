@@ -805,20 +805,30 @@ static T* at(T* const* a, int k) {
 }
 
 // End-to-end solve of several lattices with the copies beside the steps (the
-// body of trtrlb_batch_solve): uploads on `cin`, member k's init, steps and
-// moments on `st`, its downloads on `cout` once its moments are written.
-int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t cin, cudaStream_t cout,
-                  const double* const* rho, const double* const* ux, const double* const* uy, int64_t nsteps,
-                  double* const* rho_out, double* const* ux_out, double* const* uy_out, char* err) {
+// body of trtrlb_batch_solve): uploads on `cin`, member k's steps on `st`, its
+// initial state and moments on `aux` (beside the neighbouring members' steps),
+// its downloads on `cout` once its moments are written.
+int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStream_t aux, cudaStream_t cin,
+                  cudaStream_t cout, const double* const* rho, const double* const* ux, const double* const* uy,
+                  int64_t nsteps, double* const* rho_out, double* const* ux_out, double* const* uy_out,
+                  char* err) {
     if (count < 0 || (count > 0 && (!m || !ux || !uy)) || nsteps < 0)
         return fail(err, TRTRLB_EINVAL, "bad member list, input arrays or step count");
     for (int k = 0; k < count; ++k)
         if (!m[k] || !ux[k] || !uy[k]) return fail(err, TRTRLB_EINVAL, "every member needs ux and uy");
     if (count == 0) return TRTRLB_OK;
-    std::vector<cudaEvent_t> ev(2 * (size_t)count + 1, nullptr);
+    // events per member: uploaded, initialised, stepped, moments written; and one
+    // for the members' earlier work
+    std::vector<cudaEvent_t> ev(4 * (size_t)count + 1, nullptr);
+    cudaEvent_t* ev_in = ev.data();
+    cudaEvent_t* ev_init = ev.data() + count;
+    cudaEvent_t* ev_step = ev.data() + 2 * count;
+    cudaEvent_t* ev_mom = ev.data() + 3 * count;
+    cudaEvent_t ev_prior = ev[4 * (size_t)count];
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    ev_prior = ev[4 * (size_t)count];
     // staging for host inputs and outputs (allocated before any copy is queued)
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         const void* io[6] = {at(rho, k), ux[k], uy[k], at(rho_out, k), at(ux_out, k), at(uy_out, k)};
@@ -828,10 +838,9 @@ int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStre
     }
     // every member's earlier work (on its own stream) before this call's
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
-        e = cudaEventRecord(ev[2 * count], m[k]->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[2 * count], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, ev[2 * count], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev[2 * count], 0);
+        e = cudaEventRecord(ev_prior, m[k]->stream);
+        for (cudaStream_t x : {st, aux, cin, cout})
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(x, ev_prior, 0);
     }
     std::vector<const double*> din(3 * (size_t)count, nullptr);
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
@@ -845,37 +854,50 @@ int solve_members(trtrlb_lattice* const* m, int count, cudaStream_t st, cudaStre
             e = cudaMemcpyAsync(m[k]->stage + q * n, src[q], n * sizeof(double), cudaMemcpyHostToDevice, cin);
             din[3 * k + q] = m[k]->stage + q * n;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[k], cin);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], cin);
     }
+    // initial states on the auxiliary stream, each as soon as its fields are up
+    // (member k + 1's beside member k's steps)
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        trtrlb_lattice* h = m[k];
+        e = cudaStreamWaitEvent(aux, ev_in[k], 0);
+        if (e == cudaSuccess)
+            e = TRT_DISPATCH(h->p.storage, init(h->s, din[3 * k], din[3 * k + 1], din[3 * k + 2], aux));
+        if (e == cudaSuccess) e = cudaEventRecord(ev_init[k], aux);
+        h->t = 0;
+    }
+    // the steps, member after member; each member's moments on the auxiliary
+    // stream and its download on the copy stream, beside the next member's steps
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         trtrlb_lattice* h = m[k];
         const size_t n = (size_t)h->p.nx * h->p.ny;
-        e = cudaStreamWaitEvent(st, ev[k], 0);
-        if (e == cudaSuccess)
-            e = TRT_DISPATCH(h->p.storage, init(h->s, din[3 * k], din[3 * k + 1], din[3 * k + 2], st));
-        if (e != cudaSuccess) break;
-        h->t = 0;
+        e = cudaStreamWaitEvent(st, ev_init[k], 0);
         for (int64_t q = 0; q < nsteps && e == cudaSuccess; ++q) {
             e = TRT_DISPATCH(h->p.storage, step(h->s, st));
             ++h->t;
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_step[k], st);
         double* dst[3] = {at(rho_out, k), at(ux_out, k), at(uy_out, k)};
         double* dev[3] = {nullptr, nullptr, nullptr};
         for (int q = 0; q < 3; ++q)
             if (dst[q]) dev[q] = on_device(dst[q]) ? dst[q] : h->stage + q * n;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_step[k], 0);
         if (e == cudaSuccess && (dev[0] || dev[1] || dev[2]))
-            e = TRT_DISPATCH(h->p.storage, moments(h->s, dev[0], dev[1], dev[2], st));
-        if (e == cudaSuccess) e = cudaEventRecord(ev[count + k], st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev[count + k], 0);
+            e = TRT_DISPATCH(h->p.storage, moments(h->s, dev[0], dev[1], dev[2], aux));
+        if (e == cudaSuccess) e = cudaEventRecord(ev_mom[k], aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev_mom[k], 0);
         for (int q = 0; q < 3 && e == cudaSuccess; ++q)
             if (dst[q] && dev[q] != dst[q])
                 e = cudaMemcpyAsync(dst[q], dev[q], n * sizeof(double), cudaMemcpyDeviceToHost, cout);
     }
-    const cudaError_t e1 = cudaStreamSynchronize(cout), e2 = cudaStreamSynchronize(st),
-                      e3 = cudaStreamSynchronize(cin);
+    cudaError_t es = cudaSuccess;
+    for (cudaStream_t x : {cout, st, aux, cin}) {
+        const cudaError_t ex_ = cudaStreamSynchronize(x);
+        if (es == cudaSuccess) es = ex_;
+    }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
-    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    if (e == cudaSuccess) e = es;
     if (e != cudaSuccess) return cuda_fail(err, e, "solve");
     for (int k = 0; k < count; ++k)
         if (const int rc = check_kerr(m[k])) {
