@@ -423,6 +423,76 @@ __host__ __device__ constexpr int step_min_blocks() {
                                                                    : 1;
 }
 
+// The periodic step (node_step_periodic, below) in two halves, for the general
+// step's interior segments (the periodic kernels keep the single body, which
+// compiles to a faster schedule).  The reads: the nine slots and, with Phi
+// lagged, the two Phi differences.  Every index stays inside the buffers for any node of the
+// lattice (the wrap corrections keep it in its plane), which the general step
+// relies on when it issues these loads before it knows whether the node is
+// interior.
+template <typename S, bool ODD, int GMODE>
+__device__ __forceinline__ void periodic_load(const Args<typename Fmt<S>::C>& a, int x, int y,
+                                              typename Fmt<S>::C (&d)[9], typename Fmt<S>::C& dpx,
+                                              typename Fmt<S>::C& dpy) {
+    using C = typename Fmt<S>::C;
+    const int own = y * a.pitch + x;
+    const int pt = a.pitch;
+    const int pl = (int)a.plane;           // a plane holds at most 2^30 nodes
+    const int cxp = x == a.nx - 1 ? -a.nx : 0, cxm = x == 0 ? a.nx : 0;
+    const int cyp = y == a.ny - 1 ? -pl : 0, cym = y == 0 ? pl : 0;
+    const S* __restrict__ F = static_cast<const S*>(a.f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int k = ODD ? opp(i) : i;
+        int idx = own;
+        if (ODD) {
+            idx += ey(k) * pt + ex(k);
+            idx += ex(k) > 0 ? cxp : (ex(k) < 0 ? cxm : 0);
+            idx += ey(k) > 0 ? cyp : (ey(k) < 0 ? cym : 0);
+        }
+        d[i] = Fmt<S>::ld(F[(long long)k * a.plane + idx]);
+    }
+    dpx = C(0);
+    dpy = C(0);
+    if (GMODE == G_LAGGED) {
+        const C* Px = a.phi_in + own;
+        const C* Py = a.phi_in + a.plane + own;
+        dpx = C(0.5) * (Px[1 + cxp] - Px[-1 + cxm]);
+        dpy = C(0.5) * (Py[pt + cyp] - Py[-pt + cym]);
+    }
+}
+
+// Its collision and writes, from the values periodic_load read.
+template <typename S, bool ODD, int GMODE>
+__device__ __forceinline__ void periodic_finish(const Args<typename Fmt<S>::C>& a, int x, int y,
+                                                const typename Fmt<S>::C (&d)[9], typename Fmt<S>::C dpx,
+                                                typename Fmt<S>::C dpy) {
+    using C = typename Fmt<S>::C;
+    const int own = y * a.pitch + x;
+    const int pt = a.pitch;
+    const int pl = (int)a.plane;
+    const int cxp = x == a.nx - 1 ? -a.nx : 0, cxm = x == 0 ? a.nx : 0;
+    const int cyp = y == a.ny - 1 ? -pl : 0, cym = y == 0 ? pl : 0;
+    S* __restrict__ F = static_cast<S*>(a.f);
+    C o[9], phx, phy;
+    collide<C>(d, dpx, dpy, a.k1, a.k1lo, a.k2, a.k2lo, a.kf, a.gx, a.gy, a.rho0, o, phx, phy);
+    if (GMODE == G_LAGGED) {
+        a.phi_out[own] = phx;
+        a.phi_out[a.plane + own] = phy;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int k = ODD ? i : opp(i);
+        int idx = own;
+        if (ODD) {
+            idx += ey(k) * pt + ex(k);
+            idx += ex(k) > 0 ? cxp : (ex(k) < 0 ? cxm : 0);
+            idx += ey(k) > 0 ? cyp : (ey(k) < 0 ? cym : 0);
+        }
+        F[(long long)k * a.plane + idx] = Fmt<S>::st(o[i]);
+    }
+}
+
 // The step of a node of a lattice periodic in x and y, without a mask.  The
 // nine slots it reads and writes are A_k = F[k][x + e_k] on an odd level (it
 // reads f_i from A_ibar and writes f*_i to A_i) and F[k][x] on an even one
@@ -492,10 +562,24 @@ __device__ __forceinline__ void node_step(const Args<typename Fmt<S>::C>& a, int
     }
     // a row segment whose nodes and their neighbours are all plain fluid (no
     // wall, mask class or open edge on any link; a warp is one segment, so
-    // the branch is uniform): the periodic step's code, same arithmetic
-    if (a.seg && a.seg[y * a.segs + (x >> 5)]) {
-        node_step_periodic<S, ODD, GMODE>(a, x, y);
-        return;
+    // the branch is uniform): the periodic step's code, same arithmetic.  Its
+    // loads are issued together with the segment map's byte, not after it (they
+    // stay inside the buffers for any node; elsewhere their values are unused)
+    // (FP32 and 16-bit; the double-word step, issue-bound, measured faster
+    // branching first)
+    if (a.seg) {
+        if constexpr (sizeof(S) <= 4) {
+            const bool interior = a.seg[y * a.segs + (x >> 5)] != 0;
+            C dq[9], dpxq, dpyq;
+            periodic_load<S, ODD, GMODE>(a, x, y, dq, dpxq, dpyq);
+            if (interior) {
+                periodic_finish<S, ODD, GMODE>(a, x, y, dq, dpxq, dpyq);
+                return;
+            }
+        } else if (a.seg[y * a.segs + (x >> 5)]) {
+            node_step_periodic<S, ODD, GMODE>(a, x, y);
+            return;
+        }
     }
     S* __restrict__ F = static_cast<S*>(a.f);
     const int own = y * a.pitch + x;   // in-plane offsets stay below 2^30
