@@ -73,6 +73,39 @@ def test_masks_inlet_outlet_match_oracle(gpu_lib, seed, storage):
 
 
 @pytest.mark.parametrize("storage", FP64)
+@pytest.mark.parametrize("periodic", [(True, True), (False, True), (True, False)])
+def test_interior_segments_match_oracle(gpu_lib, storage, periodic):
+    """Masked and walled lattices mixing interior row segments (32 nodes whose
+    links all stay between plain fluid nodes: the general step runs the
+    periodic code there) and boundary ones: blocks that end inside a segment,
+    one across the periodic edge, a row of segments next to walls, and a
+    ragged last segment (nx = 200); every field to 1e-12 of the oracle over
+    steps of both parities."""
+    nx, ny = 200, 70
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[10:14, 40:45] = O.SOLID            # inside the second segment
+    mask[30:33, 62:66] = O.SOLID            # across a segment boundary (64)
+    mask[50:52, 196:200] = O.SOLID          # at the right edge
+    mask[50:52, 0:3] = O.SOLID              # and its periodic image side
+    if not periodic[0]:
+        mask[50:52, 0:3] = O.FLUID          # open in x: inlet and outlet columns instead
+        mask[50:52, 196:200] = O.FLUID
+        mask[50:52, 190:195] = O.SOLID      # (an outlet ghost needs fluid inward)
+        mask[:, 0] = O.INLET
+        mask[:, nx - 1] = O.OUTLET
+    pr = _random_problem(nx, ny, seed=7, periodic=periodic, g=(2e-5, -1e-5), mask=mask, wall_u=(0.02, 0.0))
+    rho, ux, uy = W.random_fields(nx, ny, seed=9)
+    G = gpu_lattice(pr, storage).init(ux, uy, rho)
+    R = oracle_lattice(pr).init(ux, uy, rho)
+    fluid = mask == O.FLUID
+    for n in (1, 1, 6):
+        G.step(n)
+        R.step(n)
+        errs = field_errors(G, R, fluid)
+        assert max(errs.values()) < 1e-12, (n, errs)
+
+
+@pytest.mark.parametrize("storage", FP64)
 @pytest.mark.parametrize("variant", ["magic", "rlb"])
 def test_taylor_green_1000_steps_fp64(gpu_lib, variant, storage):
     """64^2 Taylor-Green, u0 = 0.04, Re = 100, Lambda = 1/4 or tau2 = tau1: every
