@@ -225,6 +225,38 @@ __device__ __forceinline__ S pack_elem(const typename Pk<S>::P& p, int v) {
     return (S)Pk<S>::elem(p, v);
 }
 
+// Elements 1 .. V-1 of a pack to p[1 .. V-1], and elements 0 .. V-2 to
+// p[0 .. V-2] (p = a row + x0, x0 a multiple of V, so p is aligned to the
+// pack): for V = 4 the aligned pair of the four goes in one access.
+template <typename S>
+__device__ __forceinline__ void store_from1(S* p, const typename Pk<S>::P& w) {
+    constexpr int V = Pk<S>::V;
+    if constexpr (V == 4 && sizeof(S) == 2) {
+        p[1] = pack_elem<S>(w, 1);
+        *reinterpret_cast<unsigned int*>(p + 2) = Pk<S>::word(w, 1);
+    } else if constexpr (V == 4 && std::is_same<S, float>::value) {
+        p[1] = w.y;
+        *reinterpret_cast<float2*>(p + 2) = make_float2(w.z, w.w);
+    } else {
+#pragma unroll
+        for (int v = 1; v < V; ++v) p[v] = pack_elem<S>(w, v);
+    }
+}
+template <typename S>
+__device__ __forceinline__ void store_to_last(S* p, const typename Pk<S>::P& w) {
+    constexpr int V = Pk<S>::V;
+    if constexpr (V == 4 && sizeof(S) == 2) {
+        *reinterpret_cast<unsigned int*>(p) = Pk<S>::word(w, 0);
+        p[2] = pack_elem<S>(w, 2);
+    } else if constexpr (V == 4 && std::is_same<S, float>::value) {
+        *reinterpret_cast<float2*>(p) = make_float2(w.x, w.y);
+        p[2] = w.z;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V - 1; ++v) p[v] = pack_elem<S>(w, v);
+    }
+}
+
 // ---- the vectorised node-segment update ---------------------------------------
 // Lane `lane` of a warp owns nodes x0 .. x0 + V - 1 of row y (active when
 // x0 < nx).  All 32 lanes must call this together (warp shuffles).
@@ -336,23 +368,15 @@ __device__ __forceinline__ void seg_step(const Args<typename Fmt<S>::C>& a, int 
             } else if (dx > 0) {   // targets x0 + 1 .. x0 + V
                 const P Wv = K::shift_up(o[i], shfl_up1(K::last_word(o[i])));
                 if (active) {
-                    if (!edge_l) {
-                        st16<S>(base + x0, Wv);
-                    } else {
-#pragma unroll
-                        for (int v = 1; v < V; ++v) base[x0 + v] = pack_elem<S>(Wv, v);
-                    }
+                    if (!edge_l) st16<S>(base + x0, Wv);
+                    else store_from1<S>(base + x0, Wv);
                     if (edge_r) base[xr] = pack_elem<S>(o[i], V - 1);
                 }
             } else {               // targets x0 - 1 .. x0 + V - 2
                 const P Wv = K::shift_down(o[i], shfl_down1(K::first_word(o[i])));
                 if (active) {
-                    if (!edge_r) {
-                        st16<S>(base + x0, Wv);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < V - 1; ++v) base[x0 + v] = pack_elem<S>(Wv, v);
-                    }
+                    if (!edge_r) st16<S>(base + x0, Wv);
+                    else store_to_last<S>(base + x0, Wv);
                     if (edge_l) base[xl] = pack_elem<S>(o[i], 0);
                 }
             }
