@@ -675,7 +675,7 @@ def main():
     h2d_bytes = sum(a.numel() * a.element_size() for f in host_in for a in f if a is not None)
     d2h_bytes = sum(a.numel() * a.element_size() for f in host_out for a in f)
     e2e_times = []
-    for rep in range(0 if args.no_e2e else 5):
+    for rep in range(0 if args.no_e2e else 9):
         barrier()
         t0 = time.perf_counter()
         if args.mode == "batch":
