@@ -408,18 +408,18 @@ __device__ __forceinline__ void moments_of(const C (&d)[9], C gx, C gy, C rho0, 
 // periodic double-word step 64 (4 CTAs; the odd step took 79 and 3).  The
 // general steps (walls, masks, open edges) run the periodic code on interior
 // row segments, so their own code may spill a little: FP32 and 16-bit 6 CTAs
-// (40 registers; 12-80 bytes of spills in the boundary code), double-word 3
-// (72-80 registers, no spills).  Measured on 4096 x 2048 creeping flow and a
-// 4096^2 channel (ms per step, compiler's choice / these): FP32 0.1635 /
-// 0.1442 and 0.2984 / 0.2630, FP16 0.1316 / 0.1138 and 0.2367 / 0.2017,
-// F64_DW 0.3826 / 0.3550 and 0.8070 / 0.7558.  The other variants keep the
-// compiler's choice.
+// (40 registers; 12-80 bytes of spills in the boundary code), double-word 4
+// (64 registers, no spills with Phi lagged).  Measured on 4096 x 2048 creeping
+// flow and a 4096^2 channel (ms per step, compiler's choice / these): FP32
+// 0.1635 / 0.1442 and 0.2984 / 0.2630, FP16 0.1316 / 0.1138 and 0.2367 /
+// 0.2017, F64_DW 0.3826 / 0.3335 and 0.8070 / 0.7076 (3 CTAs: 0.3587 and
+// 0.7563).  The other variants keep the compiler's choice.
 template <typename S, bool GENERAL, int GMODE>
 __host__ __device__ constexpr int step_min_blocks() {
     return (sizeof(S) == 4 && !GENERAL && GMODE == G_LAGGED) ? 6
            : (sizeof(S) <= 4 && GENERAL)                          ? 6
            : (std::is_same<S, f64dw>::value && !GENERAL)          ? 4
-           : (std::is_same<S, f64dw>::value && GENERAL)           ? 3
+           : (std::is_same<S, f64dw>::value && GENERAL)           ? 4
                                                                    : 1;
 }
 
