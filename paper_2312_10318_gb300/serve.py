@@ -214,9 +214,11 @@ def diagnose(lats, stream) -> list:
 class PrecisionGuard:
     """Admission-time check of a reduced-precision solve against FP64.
 
-    The lattice and an FP64 shadow start from the same fields and advance a
-    short probe (at most `probe` steps, a sixteenth of the run).  The velocity
-    error against the shadow, RMS(u - u_FP64) / U with U the solve's
+    The lattice and a shadow start from the same fields and advance a short
+    probe (at most `probe` steps, a sixteenth of the run).  The shadow is FP64
+    (the format `fp64`), or FP32 for a 16-bit format whose tolerance is far
+    above FP32's own error (shadow_format).  The velocity error against the
+    shadow, RMS(u - u_shadow) / U with U the solve's
     characteristic speed (reduced in FP64 on the device), is taken at half the
     probe and at its end and fitted as e(t) = e0 + r t (e0: the one-time
     rounding of the initial state into the format; r: its growth per step); the
@@ -271,11 +273,14 @@ class PrecisionGuard:
         if lat is None:
             lat = init(make(storage))
         m = max(2, min(self.probe, steps // 16)) // 2 * 2
-        shadow = make(self.fp64)
+        shadows = {}           # format -> shadow lattice, made on first use
         cur = lat
         while storage != "f64":
             tol = self.tol if self.tol is not None else stated_bound(storage, steps)
-            init(shadow)
+            fmt = self.shadow_format(storage, tol, steps)
+            if fmt not in shadows:
+                shadows[fmt] = make(fmt)
+            shadow = init(shadows[fmt])
             e_end, pred = self._predict(steps, cur, shadow, scale, m)
             self.checked.append((rid, storage, e_end, pred, tol))
             if math.isfinite(pred) and pred <= tol:
@@ -284,13 +289,29 @@ class PrecisionGuard:
             if cur is not lat:
                 self._release(cur)
             if storage != "f64":
-                cur = init(make(storage))
+                # a shadow in the wider format is a lattice of the problem already
+                cur = init(shadows.pop(storage) if storage in shadows else make(storage))
         if storage == "f64":
-            if cur is not lat and cur is not shadow:
+            keep = shadows.pop(self.fp64, None) or make(self.fp64)
+            if cur is not lat:
                 self._release(cur)
-            return init(shadow)
-        self._release(shadow)
+            for L in shadows.values():
+                self._release(L)
+            return init(keep)
+        for L in shadows.values():
+            self._release(L)
         return init(cur)
+
+    def shadow_format(self, storage: str, tol: float, steps: int) -> str:
+        """The format the error of `storage` is measured against: FP32 for the
+        16-bit formats when the tolerance is at least 10 times FP32's own
+        stated error for that many steps (the FP32 shadow's own error then
+        moves the measured one by at most a tenth of the tolerance, and it runs
+        several times faster than an FP64-level shadow), else the FP64
+        format."""
+        if storage in ("f16", "bf16") and tol >= 10.0 * stated_bound("f32", steps):
+            return "f32"
+        return self.fp64
 
     def __call__(self, req: Request, lat):
         from .lattice import Lattice

@@ -91,3 +91,66 @@ def test_stated_bound_grows_with_the_step_count_up_to_the_cap():
     # wider formats never state a larger error for the same run
     for n in (10, 1000, 20000):
         assert S.stated_bound("f32", n) <= S.stated_bound("f16", n) <= S.stated_bound("bf16", n)
+
+
+class _FakeLattice:
+    """Stands in for a Lattice in the guard's selection: its velocity error
+    against the exact solution grows with the step count by a law per format."""
+    ERR = {"f16": lambda t: 5e-4 + 5e-6 * t, "bf16": lambda t: 2e-3 + 2e-5 * t,
+           "f32": lambda t: 1e-7 + 1e-8 * t, "f64": lambda t: 0.0, "f64dw": lambda t: 0.0}
+
+    def __init__(self, storage, log):
+        self.storage, self.t, self.log = storage, 0, log
+        log.append(("make", storage))
+
+    def step(self, n):
+        self.t += n
+        return self
+
+    def compare(self, other):
+        return {"rms_du": abs(self.ERR[self.storage](self.t) - self.ERR[other.storage](other.t)) * 0.04}
+
+
+def _select(guard, storage, steps, err=None):
+    from paper_2312_10318_gb300 import serve as S
+    log = []
+    if err:
+        _FakeLattice.ERR = dict(_FakeLattice.ERR, **err)
+    guard.release = lambda L: log.append(("release", L.storage))
+    make = lambda st: _FakeLattice(st, log)
+    def init(L):
+        L.t = 0
+        return L
+    out = guard.select(make, init, storage, steps, 0.04)
+    return out, log
+
+
+def test_guard_measures_16_bit_formats_against_fp32_when_the_tolerance_allows():
+    """The shadow of a 16-bit format is FP32 when the tolerance is at least 10x
+    FP32's own stated error for the run, else the FP64 format; a widened solve
+    reuses the FP32 shadow as its lattice; every lattice not returned is
+    released."""
+    from paper_2312_10318_gb300 import serve as S
+    saved = dict(_FakeLattice.ERR)
+    try:
+        g = S.PrecisionGuard(fp64="f64dw")
+        out, log = _select(g, "f16", 1000)                 # default bound: FP32 shadow, kept in FP16
+        assert out.storage == "f16" and ("make", "f32") in log and ("make", "f64dw") not in log
+        assert log.count(("release", "f32")) == 1
+        assert g.shadow_format("f16", S.stated_bound("f16", 1000), 1000) == "f32"
+        assert g.shadow_format("f16", 1e-4, 1000) == "f64dw"
+        assert g.shadow_format("f16", S.stated_bound("f16", 20000), 20000) == "f64dw"   # FP32's bound grows too
+        assert g.shadow_format("f32", 1.0, 1000) == "f64dw"
+        strict = S.PrecisionGuard(tol=1e-9, fp64="f64dw")  # too tight for FP32: FP64-level shadow, to f64dw
+        out, log = _select(strict, "f16", 1000)
+        assert out.storage == "f64dw" and ("make", "f32") in log
+        assert [e for e in log if e[0] == "make"].count(("make", "f64dw")) == 1
+        assert ("release", "f32") in log
+        # FP16 misses a tolerance FP32 meets: the FP32 shadow becomes the solve
+        mid = S.PrecisionGuard(tol=0.0105, fp64="f64dw")
+        out, log = _select(mid, "f16", 1000, err={"f16": lambda t: 2e-2})
+        assert out.storage == "f32"
+        assert [e for e in log if e[0] == "make"] == [("make", "f16"), ("make", "f32"), ("make", "f64dw")]
+        assert ("release", "f64dw") in log and ("release", "f32") not in log
+    finally:
+        _FakeLattice.ERR = saved
