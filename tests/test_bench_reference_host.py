@@ -98,3 +98,20 @@ def test_reference_arm_follows_the_g_mode():
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads([l for l in r.stdout.splitlines() if l.strip().startswith("{")][0])
     assert d["config"]["workload"].endswith("G current") and d["value"] > 0
+
+
+def test_walled_and_masked_workloads():
+    """The creeping-flow and channel workloads: their geometry, and the mask's
+    byte in the algorithmic bytes per node."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle as O
+    probs, st, desc = bench.workload("creeping4096x2048", size=(256, 128))
+    p = probs[0]
+    assert st == "f32" and p.periodic == (False, True) and p.mask is not None
+    assert (p.mask[:, 0] == O.INLET).all() and (p.mask[:, -1] == O.OUTLET).all()
+    assert (p.mask == O.SOLID).sum() == 64 * 64
+    probs, st, desc = bench.workload("channel4096", size=(64, 32))
+    assert probs[0].periodic == (True, False) and probs[0].mask is None and probs[0].g[0] > 0
+    assert bench.bytes_per_node("f32", "lagged", mask=True) == 89
+    assert bench.bytes_per_node("f16", "current", mask=True) == 37
